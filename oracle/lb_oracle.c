@@ -1,0 +1,542 @@
+/*
+ * Plain FP64 CPU oracle for the free-energy binary-fluid lattice Boltzmann
+ * step of Pooley, Kusumaatmaja & Yeomans, "Contact line dynamics in binary
+ * lattice Boltzmann simulations" (arXiv:0812.1282).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may link, load or
+ * call this file; only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code with the CUDA path.
+ *
+ * The code is deliberately literal and slow: one pass per algorithmic step
+ * over the whole lattice, the equilibria written with the generic
+ * e_ia e_ib sums of the Appendix, and the MRT collision as the dense
+ * 9x9 products M^-1 S M of Sec. III.B.  All arithmetic is double precision.
+ *
+ * Lattice conventions (Sec. III.A): velocities in the paper's order
+ *   e0=(0,0) e1=(1,0) e2=(-1,0) e3=(0,1) e4=(0,-1)
+ *   e5=(1,1) e6=(-1,-1) e7=(-1,1) e8=(1,-1),   c = dx = dt = 1.
+ * Arrays are [population][y][x] with x fastest, nx columns, ny rows.
+ * x is always periodic.  y is periodic (walls == 0) or bounded by mid-link
+ * bounce-back walls below row 0 and above row ny-1 (walls == 1).
+ *
+ * The stored state is the post-collision population set f'(t), g'(t).
+ * One call of orc_step advances it by: pull-stream (Eqs. stream1-2, with
+ * bounce-back), moments (Step 1, Eq. moments), derivatives (Eq. best with the
+ * wetting ghost rows), chemical potential / pressure (Eqs. chempot, p0),
+ * Step 2 (zero equilibrium velocity at boundary nodes), equilibria (Eq.
+ * equilibrium, feq0) and BGK (Eqs. latbolt, gevo) or MRT (Eqs. mrtlb, Matrix,
+ * diag) collision.
+ *
+ * Readings of points the paper leaves open (kept identical on the CUDA side
+ * by independent code):
+ *  - wetting gradient h is the inward-normal derivative of phi at a wall
+ *    (xi = kappa*h, Sec. II); a ghost row mirrors phi about the boundary row:
+ *    phi(x,-1) = phi(x,1) - 2 h_bottom, phi(x,ny) = phi(x,ny-2) - 2 h_top,
+ *    which makes the isotropic y-derivative at the boundary row equal to the
+ *    imposed inward gradient exactly;
+ *  - boundary nodes of Step 2 are the fluid rows adjacent to a wall;
+ *  - conserved-moment rates are the literal zeros of Eq. diag.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct orc_params {
+    double a, kappa;          /* psi = a(-phi^2/2 + phi^4/4), Eq. bulkfe     */
+    double gamma_mob;         /* Gamma of the g equilibrium, Eq. Mobility   */
+    double tau_phi;           /* g relaxation time, Eq. gevo                */
+    double tau_alpha;         /* tau_rho in the phi=+1 phase, Eq. tau       */
+    double tau_beta;          /* tau_rho in the phi=-1 phase, Eq. tau       */
+    double h_bottom, h_top;   /* inward normal d(phi)/dn at the walls       */
+    int collision;            /* 0 = BGK (Eq. latbolt), 1 = MRT (Eq. mrtlb) */
+    int zero_u_at_walls;      /* Step 2 of Sec. V                           */
+    int walls;                /* 1 = walls at y=0 and y=ny-1, 0 = periodic  */
+    int mrt_all_rates;        /* test mode: every S entry equal to omega    */
+} orc_params;
+
+/* ---------------------------------------------------------------- lattice */
+static const int EX[9] = {0, 1, -1, 0, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+static const int OPP[9] = {0, 2, 1, 4, 3, 6, 5, 8, 7};
+
+/* Appendix weights for i = 1..8 (index 0 unused: it follows from Eq. feq0) */
+static const double WI[9] = {0.0, 1.0 / 3, 1.0 / 3, 1.0 / 3, 1.0 / 3,
+                             1.0 / 12, 1.0 / 12, 1.0 / 12, 1.0 / 12};
+static const double WXX[9] = {0.0, 1.0 / 3, 1.0 / 3, -1.0 / 6, -1.0 / 6,
+                              -1.0 / 24, -1.0 / 24, -1.0 / 24, -1.0 / 24};
+static const double WYY[9] = {0.0, -1.0 / 6, -1.0 / 6, 1.0 / 3, 1.0 / 3,
+                              -1.0 / 24, -1.0 / 24, -1.0 / 24, -1.0 / 24};
+static const double WXY[9] = {0.0, 0.0, 0.0, 0.0, 0.0,
+                              1.0 / 4, 1.0 / 4, -1.0 / 4, -1.0 / 4};
+
+/* Eq. Matrix, rows as printed (columns follow the velocity order above). */
+static const double MM[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, -1, 0, 0, 1, -1, -1, 1},
+    {0, -2, 2, 0, 0, 1, -1, -1, 1},
+    {0, 0, 0, 1, -1, 1, -1, 1, -1},
+    {0, 0, 0, -2, 2, 1, -1, 1, -1},
+    {0, 1, 1, -1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, 1, -1, -1},
+};
+
+/* Eq. best: isotropic first derivative (x) and Laplacian, indexed
+ * [row][col] with row = dy+1 (bottom to top) and col = dx+1. */
+static const double DX_STENCIL[3][3] = {
+    {-1, 0, 1}, {-4, 0, 4}, {-1, 0, 1}};
+static const double LAP_STENCIL[3][3] = {
+    {1, 4, 1}, {4, -20, 4}, {1, 4, 1}};
+
+static int g_threads = 0;
+
+void orc_set_threads(int n) { g_threads = n; }
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* M^-1_ij = M_ji / sum_k M_jk^2 (orthogonal rows, Sec. III.B). */
+static void mrt_inverse(double minv[9][9])
+{
+    for (int j = 0; j < 9; ++j) {
+        double norm = 0.0;
+        for (int k = 0; k < 9; ++k) norm += MM[j][k] * MM[j][k];
+        for (int i = 0; i < 9; ++i) minv[i][j] = MM[j][i] / norm;
+    }
+}
+
+void orc_mrt_matrix(double* m_out, double* minv_out)
+{
+    double minv[9][9];
+    mrt_inverse(minv);
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            m_out[i * 9 + j] = MM[i][j];
+            minv_out[i * 9 + j] = minv[i][j];
+        }
+}
+
+static inline int wrap(int v, int n) { return ((v % n) + n) % n; }
+
+/* --------------------------------------------------------- equilibria */
+/* Eq. equilibrium and Eq. feq0 at one node.  u is the velocity used in the
+ * equilibrium (zero at Step-2 boundary nodes). */
+void orc_node_equilibrium(const orc_params* p, double rho, double phi,
+                          double ux, double uy, double dphix, double dphiy,
+                          double lap, double* feq, double* geq)
+{
+    const double a = p->a, kappa = p->kappa;
+    const double u[2] = {ux, uy};
+    const double d[2] = {dphix, dphiy};
+    /* Eq. p0 and Eq. chempot */
+    const double p0 = rho / 3.0 + a * (-0.5 * phi * phi + 0.75 * phi * phi * phi * phi);
+    const double mu = a * (-phi + phi * phi * phi) - kappa * lap;
+    double fsum = 0.0, gsum = 0.0;
+    for (int i = 1; i < 9; ++i) {
+        const double e[2] = {(double)EX[i], (double)EY[i]};
+        double eu = 0.0, quad = 0.0;
+        for (int al = 0; al < 2; ++al) {
+            eu += e[al] * u[al];
+            for (int be = 0; be < 2; ++be) {
+                const double delta = (al == be) ? 1.0 : 0.0;
+                quad += 1.5 * (e[al] * e[be] - delta / 3.0) * u[al] * u[be];
+            }
+        }
+        feq[i] = WI[i] * (p0 - kappa * phi * lap + rho * eu + rho * quad) +
+                 kappa * (WXX[i] * d[0] * d[0] + WYY[i] * d[1] * d[1] +
+                          WXY[i] * d[0] * d[1]);
+        geq[i] = WI[i] * (p->gamma_mob * mu + phi * eu + phi * quad);
+        fsum += feq[i];
+        gsum += geq[i];
+    }
+    feq[0] = rho - fsum;
+    geq[0] = phi - gsum;
+}
+
+/* Collision of one node's f (Eq. latbolt or Eq. mrtlb) given its
+ * equilibrium, omega = 1/tau_rho and the inverse moment matrix. */
+static void collide_f(const orc_params* p, const double minv[9][9], const double* f,
+                      const double* feq, double omega, double* fout)
+{
+    if (p->collision == 0) {
+        for (int i = 0; i < 9; ++i) fout[i] = f[i] - omega * (f[i] - feq[i]);
+        return;
+    }
+    double s[9] = {0.0, 1.0, 1.0, 0.0, 1.0, 0.0, 1.0, omega, omega}; /* Eq. diag */
+    if (p->mrt_all_rates)
+        for (int k = 0; k < 9; ++k) s[k] = omega;
+    double m[9];
+    for (int k = 0; k < 9; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < 9; ++j) acc += MM[k][j] * (f[j] - feq[j]);
+        m[k] = s[k] * acc;
+    }
+    for (int i = 0; i < 9; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += minv[i][k] * m[k];
+        fout[i] = f[i] - acc;
+    }
+}
+
+void orc_node_collide_f(const orc_params* p, const double* f, const double* feq,
+                        double omega, double* fout)
+{
+    double minv[9][9];
+    mrt_inverse(minv);
+    collide_f(p, minv, f, feq, omega, fout);
+}
+
+/* ------------------------------------------------------ phi derivatives */
+/* phi at (x, y) with the wetting ghost rows outside the walls. */
+static double phi_at(const orc_params* p, int nx, int ny, const double* phi,
+                     int x, int y)
+{
+    x = wrap(x, nx);
+    if (!p->walls) return phi[(size_t)wrap(y, ny) * nx + x];
+    if (y < 0) return phi[(size_t)1 * nx + x] - 2.0 * p->h_bottom;
+    if (y >= ny) return phi[(size_t)(ny - 2) * nx + x] - 2.0 * p->h_top;
+    return phi[(size_t)y * nx + x];
+}
+
+/* Eq. best applied at every node: d/dx, d/dy (the transpose of the printed
+ * x stencil) and the nine-point Laplacian. */
+void orc_phi_derivatives(const orc_params* p, int nx, int ny, const double* phi,
+                         double* dx, double* dy, double* lap)
+{
+    int y;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+    for (y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            double sx = 0.0, sy = 0.0, sl = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    const double v = phi_at(p, nx, ny, phi, x + c - 1, y + r - 1);
+                    sx += DX_STENCIL[r][c] * v;
+                    sy += DX_STENCIL[c][r] * v;
+                    sl += LAP_STENCIL[r][c] * v;
+                }
+            const size_t k = (size_t)y * nx + x;
+            dx[k] = sx / 12.0;
+            dy[k] = sy / 12.0;
+            lap[k] = sl / 6.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------- initial fields */
+/* Drop of radius R centred at (cx, cy), phi=+1 inside, tanh profile of width
+ * l = sqrt(2 kappa / a) (the flat-interface solution of Eq. chempot). */
+void orc_phi_drop(const orc_params* p, int nx, int ny, double R, double cx,
+                  double cy, double* phi)
+{
+    const double l = sqrt(2.0 * p->kappa / p->a);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const double d = sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy));
+            phi[(size_t)y * nx + x] = tanh((R - d) / l);
+        }
+}
+
+/* SplitMix64 (Steele, Lea & Flood 2014), used as a counter-based generator:
+ * draw k of a stream seeded with s is mix(s + (k+1) * golden_gamma). */
+static uint64_t splitmix64_draw(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) { return splitmix64_draw(seed, k); }
+
+/* phi uniform in [-amp, amp): node (x, y) takes draw k = y*nx + x. */
+void orc_phi_random(int nx, int ny, double amp, uint64_t seed, double* phi)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const uint64_t k = (uint64_t)y * (uint64_t)nx + (uint64_t)x;
+            const double u = (double)(splitmix64_draw(seed, k) >> 11) * 0x1.0p-53;
+            phi[(size_t)k] = amp * (2.0 * u - 1.0);
+        }
+}
+
+/* Initial populations: f = f^eq and g = g^eq of phi0 with rho = 1, u = 0
+ * (the stored state is post-collision; colliding an equilibrium returns it). */
+void orc_init(const orc_params* p, int nx, int ny, const double* phi0,
+              double* f, double* g)
+{
+    const size_t n = (size_t)nx * ny;
+    double* dx = malloc(n * sizeof(double));
+    double* dy = malloc(n * sizeof(double));
+    double* lap = malloc(n * sizeof(double));
+    orc_phi_derivatives(p, nx, ny, phi0, dx, dy, lap);
+    for (size_t k = 0; k < n; ++k) {
+        double feq[9], geq[9];
+        orc_node_equilibrium(p, 1.0, phi0[k], 0.0, 0.0, dx[k], dy[k], lap[k], feq, geq);
+        for (int i = 0; i < 9; ++i) {
+            f[(size_t)i * n + k] = feq[i];
+            g[(size_t)i * n + k] = geq[i];
+        }
+    }
+    free(dx);
+    free(dy);
+    free(lap);
+}
+
+/* --------------------------------------------------------- time step */
+/* Pull-stream one population set: out_i(r) = in_i(r - e_i), or the reversed
+ * own population in_opp(i)(r) when r - e_i lies in a wall (mid-link
+ * bounce-back, Sec. IV.B / Fig. 4a). */
+static void stream_pull(const orc_params* p, int nx, int ny, const double* in,
+                        double* out)
+{
+    const size_t n = (size_t)nx * ny;
+    int y;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+    for (y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            for (int i = 0; i < 9; ++i) {
+                const int sx = wrap(x - EX[i], nx);
+                int sy = y - EY[i];
+                double v;
+                if (p->walls && (sy < 0 || sy >= ny)) {
+                    v = in[(size_t)OPP[i] * n + (size_t)y * nx + x];
+                } else {
+                    sy = wrap(sy, ny);
+                    v = in[(size_t)i * n + (size_t)sy * nx + sx];
+                }
+                out[(size_t)i * n + (size_t)y * nx + x] = v;
+            }
+}
+
+static int is_boundary_node(const orc_params* p, int ny, int y)
+{
+    return p->walls && (y == 0 || y == ny - 1);
+}
+
+void orc_step(const orc_params* p, int nx, int ny, double* f, double* g, int nsteps)
+{
+    const size_t n = (size_t)nx * ny;
+    double* fs = malloc(9 * n * sizeof(double));
+    double* gs = malloc(9 * n * sizeof(double));
+    double* rho = malloc(n * sizeof(double));
+    double* phi = malloc(n * sizeof(double));
+    double* ux = malloc(n * sizeof(double));
+    double* uy = malloc(n * sizeof(double));
+    double* dx = malloc(n * sizeof(double));
+    double* dy = malloc(n * sizeof(double));
+    double* lap = malloc(n * sizeof(double));
+
+    double minv[9][9];
+    mrt_inverse(minv);
+
+    for (int s = 0; s < nsteps; ++s) {
+        /* Eqs. stream1-2 (pull form) with bounce-back */
+        stream_pull(p, nx, ny, f, fs);
+        stream_pull(p, nx, ny, g, gs);
+
+        /* Step 1: Eq. moments */
+        long long k;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+        for (k = 0; k < (long long)n; ++k) {
+            double r = 0.0, ph = 0.0, jx = 0.0, jy = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                const double fi = fs[(size_t)i * n + k];
+                r += fi;
+                jx += fi * EX[i];
+                jy += fi * EY[i];
+                ph += gs[(size_t)i * n + k];
+            }
+            rho[k] = r;
+            phi[k] = ph;
+            ux[k] = jx / r;
+            uy[k] = jy / r;
+        }
+
+        /* Eq. best with the wetting ghost rows */
+        orc_phi_derivatives(p, nx, ny, phi, dx, dy, lap);
+
+        /* Step 2, equilibria, Step 3 collision */
+        int y;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+        for (y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const size_t kk = (size_t)y * nx + x;
+                double ueqx = ux[kk], ueqy = uy[kk];
+                if (p->zero_u_at_walls && is_boundary_node(p, ny, y)) {
+                    ueqx = 0.0;
+                    ueqy = 0.0;
+                }
+                double feq[9], geq[9], fin[9], fout[9];
+                orc_node_equilibrium(p, rho[kk], phi[kk], ueqx, ueqy, dx[kk], dy[kk],
+                                     lap[kk], feq, geq);
+                /* Eq. tau */
+                const double tau = p->tau_beta +
+                                   0.5 * (phi[kk] + 1.0) * (p->tau_alpha - p->tau_beta);
+                const double omega = 1.0 / tau;
+                for (int i = 0; i < 9; ++i) fin[i] = fs[(size_t)i * n + kk];
+                collide_f(p, minv, fin, feq, omega, fout);
+                for (int i = 0; i < 9; ++i) {
+                    f[(size_t)i * n + kk] = fout[i];
+                    const double gi = gs[(size_t)i * n + kk];
+                    g[(size_t)i * n + kk] = gi - (gi - geq[i]) / p->tau_phi; /* Eq. gevo */
+                }
+            }
+        }
+    }
+    free(fs);
+    free(gs);
+    free(rho);
+    free(phi);
+    free(ux);
+    free(uy);
+    free(dx);
+    free(dy);
+    free(lap);
+}
+
+/* Observables of the stored (post-collision) state: Eq. moments. */
+void orc_moments(int nx, int ny, const double* f, const double* g, double* rho,
+                 double* phi, double* ux, double* uy)
+{
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = 0; k < n; ++k) {
+        double r = 0.0, ph = 0.0, jx = 0.0, jy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            const double fi = f[(size_t)i * n + k];
+            r += fi;
+            jx += fi * EX[i];
+            jy += fi * EY[i];
+            ph += g[(size_t)i * n + k];
+        }
+        rho[k] = r;
+        phi[k] = ph;
+        ux[k] = jx / r;
+        uy[k] = jy / r;
+    }
+}
+
+/* One time step evaluated only on the nodes of the window
+ * [x0, x1) x [y0, y1), reading a band of full-width rows
+ * [band_y0, band_y0 + band_rows) of a larger lattice (nx, ny).  The band
+ * must hold every row within two rows of the window (or reach the wall).
+ * Output arrays are [9][y1-y0][x1-x0].  Used to check sampled nodes of
+ * lattices too large for a full oracle run. */
+int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
+                    int band_rows, const double* fband, const double* gband,
+                    int x0, int x1, int y0, int y1, double* fout_w, double* gout_w)
+{
+    if (x0 < 0 || x1 > nx || x0 >= x1 || y0 < 0 || y1 > ny || y0 >= y1) return -1;
+    /* every source row of the pull must lie inside the band */
+    for (int y = y0 - 2; y <= y1 + 1; ++y) {
+        if (p->walls && (y < 0 || y >= ny)) continue;
+        const int by = (p->walls ? y : wrap(y, ny)) - band_y0;
+        if (by < 0 || by >= band_rows) return -1;
+    }
+    const size_t bn = (size_t)nx * band_rows;
+    const int wx = x1 - x0, wy = y1 - y0;
+    /* rows of the window plus a one-row ring for the stencil */
+    const int ry0 = y0 - 1, ry1 = y1 + 1;
+    const int rrows = ry1 - ry0;
+    double* fs = malloc(9 * (size_t)nx * rrows * sizeof(double));
+    double* gs = malloc(9 * (size_t)nx * rrows * sizeof(double));
+    double* phi_full = malloc((size_t)nx * rrows * sizeof(double));
+    const size_t rn = (size_t)nx * rrows;
+    double minv[9][9];
+    mrt_inverse(minv);
+    /* pull-stream the rows of interest */
+    for (int y = ry0; y < ry1; ++y) {
+        int yy = y;
+        if (!p->walls) yy = wrap(y, ny);
+        else if (y < 0 || y >= ny) continue; /* ghost rows filled below */
+        for (int x = 0; x < nx; ++x)
+            for (int i = 0; i < 9; ++i) {
+                const int sx = wrap(x - EX[i], nx);
+                int sy = yy - EY[i];
+                double fv, gv;
+                if (p->walls && (sy < 0 || sy >= ny)) {
+                    const size_t src = (size_t)OPP[i] * bn + (size_t)(yy - band_y0) * nx + x;
+                    fv = fband[src];
+                    gv = gband[src];
+                } else {
+                    sy = wrap(sy, ny);
+                    const int by = sy - band_y0;
+                    const size_t src = (size_t)i * bn + (size_t)by * nx + sx;
+                    fv = fband[src];
+                    gv = gband[src];
+                }
+                const size_t dst = (size_t)i * rn + (size_t)(y - ry0) * nx + x;
+                fs[dst] = fv;
+                gs[dst] = gv;
+            }
+    }
+    for (int y = ry0; y < ry1; ++y) {
+        if (p->walls && (y < 0 || y >= ny)) continue;
+        for (int x = 0; x < nx; ++x) {
+            double ph = 0.0;
+            for (int i = 0; i < 9; ++i) ph += gs[(size_t)i * rn + (size_t)(y - ry0) * nx + x];
+            phi_full[(size_t)(y - ry0) * nx + x] = ph;
+        }
+    }
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            /* Eq. best on the window rows; ghost rows by the wetting rule */
+            double sx = 0.0, sy = 0.0, sl = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    const int qx = wrap(x + c - 1, nx);
+                    const int qy = y + r - 1;
+                    double v;
+                    if (p->walls && qy < 0)
+                        v = phi_full[(size_t)(1 - ry0) * nx + qx] - 2.0 * p->h_bottom;
+                    else if (p->walls && qy >= ny)
+                        v = phi_full[(size_t)(ny - 2 - ry0) * nx + qx] - 2.0 * p->h_top;
+                    else
+                        v = phi_full[(size_t)(qy - ry0) * nx + qx];
+                    sx += DX_STENCIL[r][c] * v;
+                    sy += DX_STENCIL[c][r] * v;
+                    sl += LAP_STENCIL[r][c] * v;
+                }
+            const double dxv = sx / 12.0, dyv = sy / 12.0, lapv = sl / 6.0;
+            const size_t kk = (size_t)(y - ry0) * nx + x;
+            double fin[9], gin[9], r = 0.0, jx = 0.0, jy = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                fin[i] = fs[(size_t)i * rn + kk];
+                gin[i] = gs[(size_t)i * rn + kk];
+                r += fin[i];
+                jx += fin[i] * EX[i];
+                jy += fin[i] * EY[i];
+            }
+            const double ph = phi_full[kk];
+            double ueqx = jx / r, ueqy = jy / r;
+            if (p->zero_u_at_walls && is_boundary_node(p, ny, y)) {
+                ueqx = 0.0;
+                ueqy = 0.0;
+            }
+            double feq[9], geq[9], fo[9];
+            orc_node_equilibrium(p, r, ph, ueqx, ueqy, dxv, dyv, lapv, feq, geq);
+            const double tau = p->tau_beta + 0.5 * (ph + 1.0) * (p->tau_alpha - p->tau_beta);
+            collide_f(p, minv, fin, feq, 1.0 / tau, fo);
+            const size_t wk = (size_t)(y - y0) * wx + (x - x0);
+            for (int i = 0; i < 9; ++i) {
+                fout_w[(size_t)i * wx * wy + wk] = fo[i];
+                gout_w[(size_t)i * wx * wy + wk] = gin[i] - (gin[i] - geq[i]) / p->tau_phi;
+            }
+        }
+    free(fs);
+    free(gs);
+    free(phi_full);
+    return 0;
+}
