@@ -1,0 +1,210 @@
+/*
+ * lbfe.h -- C ABI of the GB300 (sm_103a) free-energy binary-fluid lattice
+ * Boltzmann library.
+ *
+ * The method is the D2Q9 binary-fluid scheme of Pooley, Kusumaatmaja &
+ * Yeomans, "Contact line dynamics in binary lattice Boltzmann simulations"
+ * (arXiv:0812.1282): a density distribution f_i and an order-parameter
+ * distribution g_i (Sec. III.A, Eq. moments), the Landau free energy of
+ * Sec. II (Eqs. freeen, bulkfe, chempot, pressten, p0), the equilibria and
+ * isotropic stencils of Appendix A (Eqs. equilibrium, feq0, best), BGK
+ * (Eqs. latbolt, gevo) or multiple-relaxation-time collision (Eqs. mrtlb,
+ * Matrix, diag) with the phi-dependent relaxation time of Eq. (tau), mid-link
+ * bounce-back walls carrying the wetting gradient d(phi)/dn (Sec. II, IV),
+ * and the four-step algorithm of Sec. V.
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: c = dx = dt = 1.  Velocity order e0=(0,0) e1=(1,0)
+ *    e2=(-1,0) e3=(0,1) e4=(0,-1) e5=(1,1) e6=(-1,-1) e7=(-1,1) e8=(1,-1).
+ *  - A domain is nx columns by ny rows (nx, ny >= 3).  x is periodic.  y is
+ *    periodic (walls = 0) or closed by mid-link bounce-back walls half a
+ *    spacing below row 0 and above row ny-1 (walls = 1).
+ *  - Host field arrays are row-major [ny][nx] doubles (x fastest);
+ *    population arrays are [9][ny][nx] doubles.
+ *  - The stored state after n steps is the post-collision population set
+ *    of step n; observables (rho, phi, u) are its moments (Eq. moments).
+ *    rho and phi equal those of the pre-collision state exactly in exact
+ *    arithmetic; so does rho*u except at Step-2 boundary nodes under BGK.
+ *  - Every call returns LB_OK (0) or a negative LB_ERR_* code and never
+ *    aborts the process; lb_last_error() gives a message for the calling
+ *    thread.  Work is enqueued on the handle's CUDA stream; calls that
+ *    return data to the host synchronise that stream first.
+ *  - The library never falls back to the CPU: without a usable CUDA device
+ *    lb_create returns LB_ERR_CUDA.
+ */
+#ifndef LBFE_H
+#define LBFE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_ERR_INVALID_ARG (-1) /* bad size, parameter, index or buffer      */
+#define LB_ERR_CUDA (-2)        /* a CUDA runtime call failed                */
+#define LB_ERR_NONFINITE (-3)   /* NaN/Inf found in the state                 */
+#define LB_ERR_TIMEOUT (-4)     /* a bounded device wait gave up              */
+#define LB_ERR_NO_INTERFACE (-5) /* fewer than 3 interface points to fit      */
+#define LB_ERR_CAPACITY (-6)    /* interface-point buffer too small           */
+
+#define LB_BGK 0 /* single relaxation time, Eq. (latbolt)                   */
+#define LB_MRT 1 /* multiple relaxation time, Eqs. (mrtlb), (Matrix), (diag) */
+
+#define LB_FP32 0 /* populations stored in FP32 as deviations from the rest
+                     state (rho = 1, u = 0, phi = 0); arithmetic in FP32 */
+#define LB_FP64 1 /* populations and arithmetic in FP64 */
+
+typedef struct lb_params {
+    double a;          /* bulk free-energy constant, psi = a(-phi^2/2 + phi^4/4), Eq. (bulkfe) */
+    double kappa;      /* gradient-energy constant, Eq. (freeen)                         */
+    double gamma_mob;  /* Gamma of the g equilibrium, Eq. (Mobility), Appendix A          */
+    double tau_phi;    /* relaxation time of g, Eq. (gevo); Sec. III.B sets 1 under MRT   */
+    double tau_alpha;  /* tau_rho in the phi = +1 phase, Eq. (tau)                        */
+    double tau_beta;   /* tau_rho in the phi = -1 phase, Eq. (tau)                        */
+    double h_bottom;   /* wetting gradient: inward-normal d(phi)/dn at the y = -1/2 wall, */
+    double h_top;      /*   and at the y = ny - 1/2 wall (xi = kappa h, Sec. II)          */
+    int collision;       /* LB_BGK or LB_MRT                                              */
+    int zero_u_at_walls; /* Step 2 of Sec. V: equilibrium velocity 0 on wall rows          */
+    int precision;       /* LB_FP32 or LB_FP64                                            */
+    int walls;           /* 1: bounce-back walls in y; 0: periodic y                      */
+} lb_params;
+
+/* Diagnostics of one domain (sums over all nodes, in FP64). */
+typedef struct lb_stats {
+    double mass;      /* sum rho                        */
+    double order;     /* sum phi                        */
+    double mom_x;     /* sum rho u_x                    */
+    double mom_y;     /* sum rho u_y                    */
+    double max_u;     /* max |u|  (spurious-current norm, Sec. IV) */
+    long long nonfinite; /* number of nodes whose moments are not finite */
+    long long step;      /* steps taken since the last initialisation  */
+} lb_stats;
+
+typedef struct lb_handle lb_handle;
+
+/* Device bytes a handle needs for n_dom domains of the given sizes and
+ * precision (state ping-pong buffers plus workspace).  Returns 0 on invalid
+ * arguments. */
+size_t lb_device_bytes(int precision, int n_dom, const int* nx, const int* ny);
+
+/* Create one domain (a batch of one).
+ *  stream:   cudaStream_t the handle enqueues on (NULL: the legacy default
+ *            stream).  The caller keeps it alive while the handle lives.
+ *  dev_mem:  optional caller-owned device buffer of at least
+ *            lb_device_bytes(...) bytes, 256-byte aligned (e.g. a PyTorch
+ *            tensor); NULL makes the library cudaMalloc and own it.
+ * Errors: LB_ERR_INVALID_ARG for nx or ny < 3, non-positive a, kappa or
+ * gamma_mob, tau_phi <= 1/2, a tau_rho(phi) <= 1/2 anywhere on
+ * phi in [-1.1, 1.1], a domain whose 9 planes exceed 2^31 elements, or a
+ * too-small dev_mem; LB_ERR_CUDA when no device is usable. */
+int lb_create(const lb_params* p, int nx, int ny, void* stream, void* dev_mem,
+              size_t dev_bytes, lb_handle** out);
+
+/* Create n_dom independent domains that advance together (one launch per
+ * step over all of them).  per_dom[d], nx[d], ny[d] describe domain d;
+ * precision and collision must be the same for all domains.  Other rules
+ * as lb_create. */
+int lb_create_batch(const lb_params* per_dom, const int* nx, const int* ny, int n_dom,
+                    void* stream, void* dev_mem, size_t dev_bytes, lb_handle** out);
+
+/* Release the handle (and the device memory it allocated itself). */
+void lb_destroy(lb_handle* h);
+
+/* Initial state of domain dom: phi0 given by one of the initialisers below,
+ * rho = 1, u = 0, and f = f^eq, g = g^eq of that state (Appendix A, with the
+ * stencils and wetting ghost rows of the domain).  Resets the step count. */
+
+/* Drop of radius R centred at (cx, cy): phi0 = tanh((R - d)/l), l =
+ * sqrt(2 kappa / a) (the flat-interface profile of Eq. chempot; width
+ * W = 2l, Sec. IV).  cy = -0.5 puts the centre on the bottom wall plane. */
+int lb_init_drop(lb_handle* h, int dom, double R, double cx, double cy);
+
+/* Spinodal start: phi0 uniform in [-amp, amp), node (x, y) taking draw
+ * k = y*nx + x of the SplitMix64 stream seeded with `seed`
+ * (mix(seed + (k+1) * 0x9E3779B97F4A7C15), top 53 bits). */
+int lb_init_random(lb_handle* h, int dom, double amp, unsigned long long seed);
+
+/* Arbitrary phi0: host (on_device = 0) or device (1) array [ny][nx] of
+ * doubles, read before the call returns. */
+int lb_init_phi(lb_handle* h, int dom, const double* phi0, int on_device);
+
+/* Advance every domain of the handle by n >= 0 time steps (Steps 1-4 of
+ * Sec. V, pull form).  Asynchronous on the handle's stream; repeated step
+ * blocks are replayed from captured CUDA graphs. */
+int lb_step(lb_handle* h, int n);
+
+/* Moments of domain dom.  rho, phi, ux, uy: [ny][nx] double buffers on the
+ * host (on_device = 0) or the device (1); any may be NULL.  stats may be
+ * NULL.  Synchronises the stream.  Returns LB_ERR_NONFINITE (after filling
+ * the outputs) if a node's moments are not finite. */
+int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi,
+               double* ux, double* uy, lb_stats* stats);
+
+/* Contact angle of a drop sitting on the bottom wall of domain dom (Sec. IV,
+ * Fig. 1): every horizontal and vertical link whose ends have phi > 0 and
+ * phi < 0 gives a phi = 0 point by linear interpolation; points closer than
+ * `exclude` to the wall plane y = -1/2 are dropped; a least-squares circle
+ * (algebraic start, geometric Gauss-Newton refinement) gives
+ * theta = 90 + asin((yc + 1/2)/R) degrees, measured through phi > 0.
+ * Any output pointer may be NULL.  LB_ERR_NO_INTERFACE if fewer than 3
+ * points remain, LB_ERR_CAPACITY if the interface is too long for the
+ * point buffer (16 (nx + ny) points). */
+int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
+                     double* R, double* xc, double* yc);
+
+/* Wetting gradient h that Eq. (theory) assigns to an equilibrium angle
+ * theta (degrees, 0..180): sqrt(2 kappa/a) h = 2 sgn(theta - 90)
+ * [cos(alpha/3)(1 - cos(alpha/3))]^(1/2), alpha = arccos(sin^2 theta).
+ * Pure host arithmetic; returns NaN for arguments out of range. */
+double lb_wetting_h(double theta_deg, double a, double kappa);
+
+/* Absolute populations of domain dom as host arrays [9][ny][nx] (FP32 state
+ * is widened to double).  Synchronises the stream. */
+int lb_get_populations(lb_handle* h, int dom, double* f, double* g);
+
+/* Rows [y0, y0 + nrows) only: host arrays [9][nrows][nx]. */
+int lb_get_populations_rows(lb_handle* h, int dom, int y0, int nrows, double* f, double* g);
+
+/* Overwrite domain dom's state with absolute populations (host arrays
+ * [9][ny][nx]); FP32 storage rounds their deviations from the rest state.
+ * The step count is left unchanged. */
+int lb_set_populations(lb_handle* h, int dom, const double* f, const double* g);
+
+/* Checkpoint: the exact device state of all domains plus the step count.
+ * lb_state_bytes gives the size; save/load copy through a host buffer of at
+ * least that size; a loaded state continues bit for bit. */
+size_t lb_state_bytes(const lb_handle* h);
+int lb_save_state(lb_handle* h, void* host_buf, size_t bytes);
+int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes);
+
+/* Launch shape: threads per CTA along x (block_x, a multiple of 32 in
+ * [32, 512]) and rows each CTA marches through (rows >= 1).  Results do not
+ * depend on it.  Invalidates captured graphs. */
+int lb_set_tile(lb_handle* h, int block_x, int rows);
+int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
+
+/* Autotuner: times each candidate launch shape for `reps` steps on the
+ * device (without advancing the state) and keeps the fastest.  Outputs may
+ * be NULL. */
+int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms);
+
+/* Steps taken since the last initialisation (host-side count). */
+long long lb_step_count(const lb_handle* h);
+
+/* Synchronise the handle's stream (LB_ERR_CUDA on a device error). */
+int lb_sync(lb_handle* h);
+
+/* Number of kernel launches this handle has enqueued so far (graph replays
+ * count every kernel node they run). */
+long long lb_launch_count(const lb_handle* h);
+
+const char* lb_error_string(int code);
+const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFE_H */

@@ -1,0 +1,893 @@
+// Host implementation of the C ABI declared in include/lbfe.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbfe.h"
+#include "lb_internal.h"
+
+using lbfe::DomDesc;
+using lbfe::StatsOut;
+using lbfe::WorkItem;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define LB_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(LB_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMinBlockX = 32;
+constexpr int kMaxBlockX = 512;
+constexpr int kGraphBig = 64;
+constexpr int kGraphSmall = 2;
+constexpr int kChunk = 1 << 20;  // nodes per staging chunk for host field output
+
+// rest-state weights of f (deviation storage): t_0 = 4/9, t_1..4 = 1/9, t_5..8 = 1/36
+const double kRest[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pitch_for(int nx, int precision)
+{
+    const int per128 = precision == LB_FP32 ? 32 : 16;  // elements per 128 bytes
+    return (nx + per128 - 1) / per128 * per128;
+}
+
+// Layout of a handle's device memory.
+struct Layout {
+    std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
+    std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
+    size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0;
+    size_t total = 0;
+    long long item_cap = 0;
+    int pts_cap = 0;
+    long long staging_nodes = 0;
+};
+
+bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout& L)
+{
+    if (n_dom < 1 || !nx || !ny) return false;
+    const size_t es = precision == LB_FP32 ? 4 : 8;
+    size_t off = 0;
+    long long max_nodes = 0, item_cap = 0, max_nx = 0;
+    int pts_cap = 0;
+    for (int d = 0; d < n_dom; ++d) {
+        if (nx[d] < 3 || ny[d] < 3) return false;
+        const long long plane = (long long)pitch_for(nx[d], precision) * ny[d];
+        if (9 * plane >= (1LL << 31)) return false;
+        const size_t buf = align_up(size_t(18) * size_t(plane) * es, kAlign);
+        L.dom_off.push_back(off);
+        L.dom_bytes.push_back(buf);
+        off += 2 * buf;
+        max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
+        max_nx = std::max<long long>(max_nx, nx[d]);
+        item_cap += (long long)((nx[d] + kMinBlockX - 1) / kMinBlockX) * ny[d];
+        pts_cap = std::max(pts_cap, 16 * (nx[d] + ny[d]));
+    }
+    L.item_cap = item_cap;
+    L.pts_cap = pts_cap;
+    // at least one full row, so host field output can always go row by row
+    L.staging_nodes = std::max(std::min<long long>(max_nodes, kChunk), max_nx);
+    L.descs = off;
+    off = align_up(off + sizeof(DomDesc) * n_dom, kAlign);
+    L.items = off;
+    off = align_up(off + sizeof(WorkItem) * (n_dom > 1 ? item_cap : 1), kAlign);
+    L.partials = off;
+    off = align_up(off + sizeof(double) * lbfe::kStatsFields * lbfe::max_partials_needed(0, 0),
+                   kAlign);
+    L.stats = off;
+    off = align_up(off + sizeof(StatsOut), kAlign);
+    L.pts = off;
+    off = align_up(off + sizeof(double) * 2 * pts_cap, kAlign);
+    L.count = off;
+    off = align_up(off + sizeof(int), kAlign);
+    L.staging = off;
+    off = align_up(off + sizeof(double) * 4 * L.staging_nodes, kAlign);
+    L.total = off;
+    return true;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate(const lb_params* p)
+{
+    if (!p) return fail(LB_ERR_INVALID_ARG, "params is NULL");
+    if (!finite_pos(p->a) || !finite_pos(p->kappa) || !finite_pos(p->gamma_mob))
+        return fail(LB_ERR_INVALID_ARG, "a, kappa and gamma_mob must be finite and > 0");
+    if (!std::isfinite(p->tau_phi) || p->tau_phi <= 0.5)
+        return fail(LB_ERR_INVALID_ARG, "tau_phi must be > 1/2");
+    if (!std::isfinite(p->tau_alpha) || !std::isfinite(p->tau_beta))
+        return fail(LB_ERR_INVALID_ARG, "tau_alpha / tau_beta must be finite");
+    for (double ph : {-1.1, 1.1}) {
+        const double tau = p->tau_beta + 0.5 * (ph + 1.0) * (p->tau_alpha - p->tau_beta);
+        if (tau <= 0.5)
+            return fail(LB_ERR_INVALID_ARG, "tau_rho(phi=%g) = %g <= 1/2", ph, tau);
+    }
+    if (!std::isfinite(p->h_bottom) || !std::isfinite(p->h_top))
+        return fail(LB_ERR_INVALID_ARG, "wetting gradients must be finite");
+    if (p->collision != LB_BGK && p->collision != LB_MRT)
+        return fail(LB_ERR_INVALID_ARG, "collision must be LB_BGK or LB_MRT");
+    if (p->precision != LB_FP32 && p->precision != LB_FP64)
+        return fail(LB_ERR_INVALID_ARG, "precision must be LB_FP32 or LB_FP64");
+    if (p->walls != 0 && p->walls != 1) return fail(LB_ERR_INVALID_ARG, "walls must be 0 or 1");
+    return LB_OK;
+}
+
+}  // namespace
+
+struct lb_handle {
+    int n_dom = 0;
+    int precision = 0, coll = 0;
+    std::vector<lb_params> params;
+    std::vector<DomDesc> descs;
+    Layout L;
+    unsigned char* base = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    int block_x = 128, rows = 32;
+    int grid_persistent = 0;  // 0: one CTA per work item
+    int schedule = 0;         // 0 domain order, 1 largest domain first
+    int n_items = 0;
+    int parity = 0;
+    long long steps = 0;
+    long long launches = 0;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (length, start parity)
+    std::vector<double> host_pts;
+
+    DomDesc* d_descs() const { return reinterpret_cast<DomDesc*>(base + L.descs); }
+    WorkItem* d_items() const { return reinterpret_cast<WorkItem*>(base + L.items); }
+    double* d_partials() const { return reinterpret_cast<double*>(base + L.partials); }
+    StatsOut* d_stats() const { return reinterpret_cast<StatsOut*>(base + L.stats); }
+    double* d_pts() const { return reinterpret_cast<double*>(base + L.pts); }
+    int* d_count() const { return reinterpret_cast<int*>(base + L.count); }
+    double* d_staging() const { return reinterpret_cast<double*>(base + L.staging); }
+    size_t elem() const { return precision == LB_FP32 ? 4 : 8; }
+};
+
+namespace {
+
+void clear_graphs(lb_handle* h)
+{
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+// Work list for the batched kernel: every (domain, x strip, row block).
+int build_items(lb_handle* h)
+{
+    if (h->n_dom == 1) {
+        h->n_items = 0;
+        return LB_OK;
+    }
+    std::vector<int> order(h->n_dom);
+    for (int d = 0; d < h->n_dom; ++d) order[d] = d;
+    if (h->schedule == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)h->descs[a].nx * h->descs[a].ny >
+                   (long long)h->descs[b].nx * h->descs[b].ny;
+        });
+    std::vector<WorkItem> items;
+    for (int d : order) {
+        const DomDesc& D = h->descs[d];
+        for (int y0 = 0; y0 < D.ny; y0 += h->rows)
+            for (int x0 = 0; x0 < D.nx; x0 += h->block_x)
+                items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0)});
+    }
+    if ((long long)items.size() > h->L.item_cap)
+        return fail(LB_ERR_INVALID_ARG, "work list exceeds its capacity");
+    h->n_items = int(items.size());
+    LB_CUDA(cudaMemcpyAsync(h->d_items(), items.data(), sizeof(WorkItem) * items.size(),
+                            cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
+{
+    const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
+                                    h->n_dom > 1 ? h->d_items() : nullptr, h->n_items, h->n_dom,
+                                    parity, h->block_x, h->rows, h->grid_persistent, s);
+    if (e != 0)
+        return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    return LB_OK;
+}
+
+int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
+{
+    auto key = std::make_pair(len, parity);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return LB_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    LB_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LB_OK;
+    for (int k = 0; k < len && rc == LB_OK; ++k) rc = enqueue_step(h, parity ^ (k & 1), h->cap_stream);
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc != LB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess) return fail(LB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return fail(LB_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+    h->graphs[key] = exec;
+    *out = exec;
+    return LB_OK;
+}
+
+// Make the handle's device current for this runtime (it keeps its own
+// notion of the current device, separate from other runtimes in the process).
+int use_device(const lb_handle* h)
+{
+    if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
+    const cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, "cudaSetDevice failed: %s", cudaGetErrorString(e));
+    return LB_OK;
+}
+
+int check_dom(const lb_handle* h, int dom)
+{
+    if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
+    if (dom < 0 || dom >= h->n_dom) return fail(LB_ERR_INVALID_ARG, "domain %d out of range", dom);
+    return use_device(h);
+}
+
+// phi0 scratch: the idle ping-pong buffer of the domain, read as doubles
+double* phi0_scratch(lb_handle* h, int dom)
+{
+    return static_cast<double*>(h->descs[dom].f[h->parity ^ 1]);
+}
+
+int finish_init(lb_handle* h, int dom)
+{
+    // every domain of a handle shares one parity; the new state goes to the
+    // current buffer, phi0 sat in the other one
+    const int e = lbfe::launch_init_eq(h->precision, h->descs[dom], phi0_scratch(h, dom),
+                                       h->parity, h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    h->steps = 0;
+    return LB_OK;
+}
+
+int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_dom, void* stream,
+                void* dev_mem, size_t dev_bytes, lb_handle** out)
+{
+    if (!out) return fail(LB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_dom < 1 || !per_dom || !nx || !ny) return fail(LB_ERR_INVALID_ARG, "bad domain list");
+    for (int d = 0; d < n_dom; ++d) {
+        const int rc = validate(&per_dom[d]);
+        if (rc != LB_OK) return rc;
+        if (per_dom[d].precision != per_dom[0].precision || per_dom[d].collision != per_dom[0].collision)
+            return fail(LB_ERR_INVALID_ARG, "precision and collision must match across a batch");
+        if (nx[d] < 3 || ny[d] < 3) return fail(LB_ERR_INVALID_ARG, "domain %d smaller than 3x3", d);
+    }
+    Layout L;
+    if (!build_layout(per_dom[0].precision, n_dom, nx, ny, L))
+        return fail(LB_ERR_INVALID_ARG, "domain too large (9 planes must stay below 2^31 elements)");
+    if (dev_mem && (dev_bytes < L.total || (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) != 0))
+        return fail(LB_ERR_INVALID_ARG, "dev_mem must be %zu bytes, 256-byte aligned", L.total);
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1)
+        return fail(LB_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+
+    int device = 0;
+    if (dev_mem) {
+        cudaPointerAttributes attr{};
+        e = cudaPointerGetAttributes(&attr, dev_mem);
+        if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice)
+            return fail(LB_ERR_INVALID_ARG, "dev_mem is not device memory");
+        device = attr.device;
+    } else if ((e = cudaGetDevice(&device)) != cudaSuccess) {
+        return fail(LB_ERR_CUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaSetDevice(device)) != cudaSuccess)
+        return fail(LB_ERR_CUDA, "cudaSetDevice(%d) failed: %s", device, cudaGetErrorString(e));
+
+    lb_handle* h = new lb_handle();
+    h->device = device;
+    h->n_dom = n_dom;
+    h->precision = per_dom[0].precision;
+    h->coll = per_dom[0].collision;
+    h->params.assign(per_dom, per_dom + n_dom);
+    h->L = L;
+    h->stream = static_cast<cudaStream_t>(stream);
+    auto bail = [&](int rc) {
+        lb_destroy(h);
+        return rc;
+    };
+    if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
+            cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(fail(LB_ERR_CUDA, "device setup failed: %s", cudaGetErrorString(e)));
+    if (dev_mem) {
+        h->base = static_cast<unsigned char*>(dev_mem);
+        h->owns = false;
+    } else {
+        void* p = nullptr;
+        if ((e = cudaMalloc(&p, L.total)) != cudaSuccess)
+            return bail(fail(LB_ERR_CUDA, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e)));
+        h->base = static_cast<unsigned char*>(p);
+        h->owns = true;
+    }
+    for (int d = 0; d < n_dom; ++d) {
+        const lb_params& p = per_dom[d];
+        DomDesc D{};
+        const int pitch = pitch_for(nx[d], h->precision);
+        D.nx = nx[d];
+        D.ny = ny[d];
+        D.pitch = pitch;
+        D.plane = (long long)pitch * ny[d];
+        const size_t half = size_t(9) * size_t(D.plane) * h->elem();
+        for (int b = 0; b < 2; ++b) {
+            unsigned char* buf = h->base + L.dom_off[d] + b * L.dom_bytes[d];
+            D.f[b] = buf;
+            D.g[b] = buf + half;
+        }
+        D.walls = p.walls;
+        D.step2 = p.zero_u_at_walls ? 1 : 0;
+        D.a = p.a;
+        D.kappa = p.kappa;
+        D.gamma = p.gamma_mob;
+        D.omega_phi = 1.0 / p.tau_phi;
+        D.tau_c0 = p.tau_beta + 0.5 * (p.tau_alpha - p.tau_beta);
+        D.tau_c1 = 0.5 * (p.tau_alpha - p.tau_beta);
+        D.h_bot = p.h_bottom;
+        D.h_top = p.h_top;
+        h->descs.push_back(D);
+    }
+    if ((e = cudaMemsetAsync(h->base, 0, L.total, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_descs(), h->descs.data(), sizeof(DomDesc) * n_dom,
+                             cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return bail(fail(LB_ERR_CUDA, "device init failed: %s", cudaGetErrorString(e)));
+    // default launch shape: 128 threads x 32 rows (tuned by lb_autotune)
+    h->block_x = 128;
+    h->rows = 32;
+    if (n_dom > 1) h->grid_persistent = h->sm_count * 8;
+    const int rc = build_items(h);
+    if (rc != LB_OK) return bail(rc);
+    *out = h;
+    return LB_OK;
+}
+
+// Least-squares circle: algebraic (Kasa) fit, then Gauss-Newton on the
+// geometric residuals.  Coordinates are centred for conditioning.
+bool solve3(double A[3][3], double b[3], double x[3])
+{
+    double M[3][4];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
+        M[i][3] = b[i];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+        if (std::fabs(M[piv][c]) < 1e-300) return false;
+        if (piv != c)
+            for (int j = 0; j < 4; ++j) std::swap(M[c][j], M[piv][j]);
+        for (int r = 0; r < 3; ++r) {
+            if (r == c) continue;
+            const double f = M[r][c] / M[c][c];
+            for (int j = c; j < 4; ++j) M[r][j] -= f * M[c][j];
+        }
+    }
+    for (int i = 0; i < 3; ++i) x[i] = M[i][3] / M[i][i];
+    return true;
+}
+
+bool fit_circle(const std::vector<double>& pts, double& xc, double& yc, double& R)
+{
+    const size_t n = pts.size() / 2;
+    double mx = 0, my = 0;
+    for (size_t i = 0; i < n; ++i) {
+        mx += pts[2 * i];
+        my += pts[2 * i + 1];
+    }
+    mx /= double(n);
+    my /= double(n);
+    double A[3][3] = {{0}}, b[3] = {0}, s[3];
+    for (size_t i = 0; i < n; ++i) {
+        const double x = pts[2 * i] - mx, y = pts[2 * i + 1] - my;
+        const double row[3] = {x, y, 1.0}, r = x * x + y * y;
+        for (int j = 0; j < 3; ++j) {
+            for (int k = 0; k < 3; ++k) A[j][k] += row[j] * row[k];
+            b[j] += row[j] * r;
+        }
+    }
+    if (!solve3(A, b, s)) return false;
+    double cx = s[0] / 2, cy = s[1] / 2;
+    double rr = std::sqrt(std::max(s[2] + cx * cx + cy * cy, 0.0));
+    for (int it = 0; it < 10; ++it) {
+        double JtJ[3][3] = {{0}}, Jtr[3] = {0}, d[3];
+        for (size_t i = 0; i < n; ++i) {
+            const double dx = pts[2 * i] - mx - cx, dy = pts[2 * i + 1] - my - cy;
+            const double dist = std::sqrt(dx * dx + dy * dy);
+            const double res = dist - rr;
+            const double J[3] = {-dx / dist, -dy / dist, -1.0};
+            for (int j = 0; j < 3; ++j) {
+                for (int k = 0; k < 3; ++k) JtJ[j][k] += J[j] * J[k];
+                Jtr[j] -= J[j] * res;
+            }
+        }
+        if (!solve3(JtJ, Jtr, d)) break;
+        cx += d[0];
+        cy += d[1];
+        rr += d[2];
+    }
+    xc = cx + mx;
+    yc = cy + my;
+    R = rr;
+    return std::isfinite(xc) && std::isfinite(yc) && std::isfinite(R) && R > 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_device_bytes(int precision, int n_dom, const int* nx, const int* ny)
+{
+    if (precision != LB_FP32 && precision != LB_FP64) return 0;
+    Layout L;
+    if (!build_layout(precision, n_dom, nx, ny, L)) return 0;
+    return L.total;
+}
+
+int lb_create(const lb_params* p, int nx, int ny, void* stream, void* dev_mem, size_t dev_bytes,
+              lb_handle** out)
+{
+    return make_handle(p, &nx, &ny, 1, stream, dev_mem, dev_bytes, out);
+}
+
+int lb_create_batch(const lb_params* per_dom, const int* nx, const int* ny, int n_dom, void* stream,
+                    void* dev_mem, size_t dev_bytes, lb_handle** out)
+{
+    return make_handle(per_dom, nx, ny, n_dom, stream, dev_mem, dev_bytes, out);
+}
+
+void lb_destroy(lb_handle* h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    clear_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->owns && h->base) cudaFree(h->base);
+    delete h;
+}
+
+int lb_init_drop(lb_handle* h, int dom, double R, double cx, double cy)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!std::isfinite(R) || !std::isfinite(cx) || !std::isfinite(cy))
+        return fail(LB_ERR_INVALID_ARG, "drop geometry must be finite");
+    const int e = lbfe::launch_init_phi_drop(h->precision, h->descs[dom], phi0_scratch(h, dom), R,
+                                             cx, cy, h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    return finish_init(h, dom);
+}
+
+int lb_init_random(lb_handle* h, int dom, double amp, unsigned long long seed)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!std::isfinite(amp)) return fail(LB_ERR_INVALID_ARG, "amp must be finite");
+    const int e = lbfe::launch_init_phi_random(h->precision, h->descs[dom], phi0_scratch(h, dom),
+                                               amp, seed, h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    return finish_init(h, dom);
+}
+
+int lb_init_phi(lb_handle* h, int dom, const double* phi0, int on_device)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!phi0) return fail(LB_ERR_INVALID_ARG, "phi0 is NULL");
+    const DomDesc& D = h->descs[dom];
+    LB_CUDA(cudaMemcpy2DAsync(phi0_scratch(h, dom), sizeof(double) * D.pitch, phi0,
+                              sizeof(double) * D.nx, sizeof(double) * D.nx, D.ny,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              h->stream));
+    rc = finish_init(h, dom);
+    if (rc != LB_OK) return rc;
+    LB_CUDA(cudaStreamSynchronize(h->stream));  // phi0 may be released by the caller
+    return LB_OK;
+}
+
+int lb_step(lb_handle* h, int n)
+{
+    if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
+    if (n < 0) return fail(LB_ERR_INVALID_ARG, "n must be >= 0");
+    if (use_device(h) != LB_OK) return LB_ERR_CUDA;
+    while (n > 0) {
+        int len = n >= kGraphBig ? kGraphBig : (n >= kGraphSmall ? kGraphSmall : 1);
+        if (len == 1) {
+            const int rc = enqueue_step(h, h->parity, h->stream);
+            if (rc != LB_OK) return rc;
+        } else {
+            cudaGraphExec_t g = nullptr;
+            const int rc = get_graph(h, len, h->parity, &g);
+            if (rc != LB_OK) return rc;
+            LB_CUDA(cudaGraphLaunch(g, h->stream));
+        }
+        if (len & 1) h->parity ^= 1;
+        h->steps += len;
+        h->launches += len;
+        n -= len;
+    }
+    return LB_OK;
+}
+
+int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi, double* ux,
+               double* uy, lb_stats* stats)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    const DomDesc& D = h->descs[dom];
+    if (stats) {
+        const int e = lbfe::launch_moments(h->precision, D, h->parity, 0, D.ny, nullptr, nullptr,
+                                           nullptr, nullptr, D.nx, h->d_partials(),
+                                           lbfe::max_partials_needed(0, 0), h->d_stats(), h->stream);
+        if (e != 0) return fail(LB_ERR_CUDA, "moments launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+        h->launches += 2;
+    }
+    double* outs[4] = {rho, phi, ux, uy};
+    const bool any = rho || phi || ux || uy;
+    if (any && on_device) {
+        const int e = lbfe::launch_moments(h->precision, D, h->parity, 0, D.ny, rho, phi, ux, uy,
+                                           D.nx, nullptr, 0, nullptr, h->stream);
+        if (e != 0) return fail(LB_ERR_CUDA, "moments launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+        h->launches += 1;
+    } else if (any) {
+        const int chunk_rows = int(std::max<long long>(1, h->L.staging_nodes / D.nx));
+        double* st = h->d_staging();
+        const long long sn = h->L.staging_nodes;
+        for (int r0 = 0; r0 < D.ny; r0 += chunk_rows) {
+            const int nr = std::min(chunk_rows, D.ny - r0);
+            double* dev[4];
+            for (int k = 0; k < 4; ++k) dev[k] = outs[k] ? st + k * sn : nullptr;
+            const int e = lbfe::launch_moments(h->precision, D, h->parity, r0, nr, dev[0], dev[1],
+                                               dev[2], dev[3], D.nx, nullptr, 0, nullptr, h->stream);
+            if (e != 0) return fail(LB_ERR_CUDA, "moments launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+            h->launches += 1;
+            for (int k = 0; k < 4; ++k)
+                if (outs[k])
+                    LB_CUDA(cudaMemcpyAsync(outs[k] + (long long)r0 * D.nx, dev[k],
+                                            sizeof(double) * nr * D.nx, cudaMemcpyDeviceToHost,
+                                            h->stream));
+        }
+    }
+    StatsOut so{};
+    if (stats)
+        LB_CUDA(cudaMemcpyAsync(&so, h->d_stats(), sizeof(StatsOut), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    if (stats) {
+        stats->mass = so.mass;
+        stats->order = so.order;
+        stats->mom_x = so.mom_x;
+        stats->mom_y = so.mom_y;
+        stats->max_u = so.max_u;
+        stats->nonfinite = (long long)so.nonfinite;
+        stats->step = h->steps;
+        if (so.nonfinite > 0)
+            return fail(LB_ERR_NONFINITE, "%lld nodes with non-finite moments", stats->nonfinite);
+    }
+    return LB_OK;
+}
+
+int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg, double* R,
+                     double* xc, double* yc)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!std::isfinite(exclude)) return fail(LB_ERR_INVALID_ARG, "exclude must be finite");
+    const DomDesc& D = h->descs[dom];
+    const int cap = 16 * (D.nx + D.ny);
+    const int e = lbfe::launch_crossings(h->precision, D, h->parity, h->d_pts(), h->d_count(), cap,
+                                         h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "crossings launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    int count = 0;
+    LB_CUDA(cudaMemcpyAsync(&count, h->d_count(), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    if (count > cap) return fail(LB_ERR_CAPACITY, "%d interface points exceed capacity %d", count, cap);
+    std::vector<double> raw(2 * size_t(count));
+    if (count > 0) {
+        LB_CUDA(cudaMemcpyAsync(raw.data(), h->d_pts(), sizeof(double) * 2 * count,
+                                cudaMemcpyDeviceToHost, h->stream));
+        LB_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    std::vector<std::pair<double, double>> pts;
+    const double wall = -0.5;
+    for (int i = 0; i < count; ++i)
+        if (raw[2 * i + 1] >= wall + exclude) pts.emplace_back(raw[2 * i], raw[2 * i + 1]);
+    std::sort(pts.begin(), pts.end());
+    if (pts.size() < 3) return fail(LB_ERR_NO_INTERFACE, "only %zu interface points", pts.size());
+    std::vector<double> flat;
+    flat.reserve(2 * pts.size());
+    for (auto& q : pts) {
+        flat.push_back(q.first);
+        flat.push_back(q.second);
+    }
+    double cx, cy, rr;
+    if (!fit_circle(flat, cx, cy, rr)) return fail(LB_ERR_NO_INTERFACE, "circle fit failed");
+    const double s = std::max(-1.0, std::min(1.0, (cy - wall) / rr));
+    if (theta_deg) *theta_deg = 90.0 + std::asin(s) * 180.0 / M_PI;
+    if (R) *R = rr;
+    if (xc) *xc = cx;
+    if (yc) *yc = cy;
+    return LB_OK;
+}
+
+double lb_wetting_h(double theta_deg, double a, double kappa)
+{
+    if (!(theta_deg >= 0.0 && theta_deg <= 180.0) || !(a > 0.0) || !(kappa > 0.0)) return NAN;
+    const double th = theta_deg * M_PI / 180.0;
+    const double s = std::sin(th);
+    const double alpha = std::acos(std::min(1.0, s * s));
+    const double c = std::cos(alpha / 3.0);
+    const double sgn = theta_deg > 90.0 ? 1.0 : (theta_deg < 90.0 ? -1.0 : 0.0);
+    return 2.0 * sgn * std::sqrt(std::max(c * (1.0 - c), 0.0)) / std::sqrt(2.0 * kappa / a);
+}
+
+int lb_get_populations_rows(lb_handle* h, int dom, int y0, int nrows, double* f, double* g)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!f && !g) return fail(LB_ERR_INVALID_ARG, "f and g are NULL");
+    const DomDesc& D = h->descs[dom];
+    if (y0 < 0 || nrows < 1 || y0 + nrows > D.ny) return fail(LB_ERR_INVALID_ARG, "bad row range");
+    const size_t nn = size_t(D.nx) * nrows, es = h->elem();
+    std::vector<unsigned char> tmp(nn * es);
+    for (int which = 0; which < 2; ++which) {
+        double* out = which == 0 ? f : g;
+        if (!out) continue;
+        const unsigned char* src =
+            static_cast<const unsigned char*>(which == 0 ? D.f[h->parity] : D.g[h->parity]);
+        for (int i = 0; i < 9; ++i) {
+            const unsigned char* plane = src + (size_t(i) * D.plane + size_t(y0) * D.pitch) * es;
+            LB_CUDA(cudaMemcpy2DAsync(tmp.data(), es * D.nx, plane, es * D.pitch, es * D.nx, nrows,
+                                      cudaMemcpyDeviceToHost, h->stream));
+            LB_CUDA(cudaStreamSynchronize(h->stream));
+            const double rest = which == 0 ? kRest[i] : 0.0;
+            double* o = out + i * nn;
+            if (es == 4) {
+                const float* t = reinterpret_cast<const float*>(tmp.data());
+                for (size_t k = 0; k < nn; ++k) o[k] = rest + double(t[k]);
+            } else {
+                const double* t = reinterpret_cast<const double*>(tmp.data());
+                for (size_t k = 0; k < nn; ++k) o[k] = rest + t[k];
+            }
+        }
+    }
+    return LB_OK;
+}
+
+int lb_get_populations(lb_handle* h, int dom, double* f, double* g)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    return lb_get_populations_rows(h, dom, 0, h->descs[dom].ny, f, g);
+}
+
+int lb_set_populations(lb_handle* h, int dom, const double* f, const double* g)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!f || !g) return fail(LB_ERR_INVALID_ARG, "f and g are required");
+    const DomDesc& D = h->descs[dom];
+    const size_t nn = size_t(D.nx) * D.ny, es = h->elem();
+    std::vector<unsigned char> tmp(9 * nn * es);
+    for (int which = 0; which < 2; ++which) {
+        const double* in = which == 0 ? f : g;
+        for (int i = 0; i < 9; ++i) {
+            const double rest = which == 0 ? kRest[i] : 0.0;
+            for (size_t k = 0; k < nn; ++k) {
+                const size_t q = i * nn + k;
+                const double v = in[q] - rest;
+                if (es == 4)
+                    reinterpret_cast<float*>(tmp.data())[q] = float(v);
+                else
+                    reinterpret_cast<double*>(tmp.data())[q] = v;
+            }
+        }
+        void* dst = which == 0 ? D.f[h->parity] : D.g[h->parity];
+        LB_CUDA(cudaMemcpy2DAsync(dst, es * D.pitch, tmp.data(), es * D.nx, es * D.nx, 9 * D.ny,
+                                  cudaMemcpyHostToDevice, h->stream));
+        LB_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return LB_OK;
+}
+
+size_t lb_state_bytes(const lb_handle* h)
+{
+    if (!h) return 0;
+    size_t total = 4 * sizeof(long long);
+    for (int d = 0; d < h->n_dom; ++d) total += size_t(18) * size_t(h->descs[d].plane) * h->elem();
+    return total;
+}
+
+int lb_save_state(lb_handle* h, void* host_buf, size_t bytes)
+{
+    if (!h || !host_buf) return fail(LB_ERR_INVALID_ARG, "NULL argument");
+    if (use_device(h) != LB_OK) return LB_ERR_CUDA;
+    if (bytes < lb_state_bytes(h)) return fail(LB_ERR_INVALID_ARG, "buffer too small");
+    long long* hdr = static_cast<long long*>(host_buf);
+    hdr[0] = 0x4c4246454348LL;  // magic
+    hdr[1] = h->n_dom;
+    hdr[2] = h->precision;
+    hdr[3] = h->steps;
+    unsigned char* p = static_cast<unsigned char*>(host_buf) + 4 * sizeof(long long);
+    for (int d = 0; d < h->n_dom; ++d) {
+        const size_t half = size_t(9) * size_t(h->descs[d].plane) * h->elem();
+        LB_CUDA(cudaMemcpyAsync(p, h->descs[d].f[h->parity], half, cudaMemcpyDeviceToHost, h->stream));
+        LB_CUDA(cudaMemcpyAsync(p + half, h->descs[d].g[h->parity], half, cudaMemcpyDeviceToHost,
+                                h->stream));
+        p += 2 * half;
+    }
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes)
+{
+    if (!h || !host_buf) return fail(LB_ERR_INVALID_ARG, "NULL argument");
+    if (use_device(h) != LB_OK) return LB_ERR_CUDA;
+    if (bytes < lb_state_bytes(h)) return fail(LB_ERR_INVALID_ARG, "buffer too small");
+    const long long* hdr = static_cast<const long long*>(host_buf);
+    if (hdr[0] != 0x4c4246454348LL || hdr[1] != h->n_dom || hdr[2] != h->precision)
+        return fail(LB_ERR_INVALID_ARG, "checkpoint does not match this handle");
+    const unsigned char* p = static_cast<const unsigned char*>(host_buf) + 4 * sizeof(long long);
+    for (int d = 0; d < h->n_dom; ++d) {
+        const size_t half = size_t(9) * size_t(h->descs[d].plane) * h->elem();
+        LB_CUDA(cudaMemcpyAsync(h->descs[d].f[h->parity], p, half, cudaMemcpyHostToDevice, h->stream));
+        LB_CUDA(cudaMemcpyAsync(h->descs[d].g[h->parity], p + half, half, cudaMemcpyHostToDevice,
+                                h->stream));
+        p += 2 * half;
+    }
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    h->steps = hdr[3];
+    return LB_OK;
+}
+
+int lb_set_tile(lb_handle* h, int block_x, int rows)
+{
+    if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
+    if (block_x < kMinBlockX || block_x > kMaxBlockX || block_x % 32 != 0 || rows < 1)
+        return fail(LB_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 512], rows >= 1");
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    h->block_x = block_x;
+    h->rows = rows;
+    return build_items(h);
+}
+
+int lb_get_tile(const lb_handle* h, int* block_x, int* rows)
+{
+    if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
+    if (block_x) *block_x = h->block_x;
+    if (rows) *rows = h->rows;
+    return LB_OK;
+}
+
+int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms)
+{
+    if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
+    if (reps < 1) reps = 1;
+    int max_ny = 0;
+    for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
+    const int bxs[] = {64, 128, 256, 512};
+    const int rws[] = {4, 8, 16, 32, 64, 128};
+    cudaEvent_t e0, e1;
+    LB_CUDA(cudaEventCreate(&e0));
+    LB_CUDA(cudaEventCreate(&e1));
+    const int old_bx = h->block_x, old_rows = h->rows;
+    double best = 1e300;
+    int bb = old_bx, br = old_rows;
+    int rc = LB_OK;
+    for (int bx : bxs) {
+        for (int r : rws) {
+            if (r > max_ny && r != rws[0]) continue;
+            if ((rc = lb_set_tile(h, bx, r)) != LB_OK) break;
+            // warm-up, then time `reps` launches that read the current buffer
+            // and write the idle one (the state itself does not advance)
+            if ((rc = enqueue_step(h, h->parity, h->stream)) != LB_OK) break;
+            cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < reps && rc == LB_OK; ++k) rc = enqueue_step(h, h->parity, h->stream);
+            cudaEventRecord(e1, h->stream);
+            if (rc != LB_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(LB_ERR_CUDA, "autotune timing failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            h->launches += reps + 1;
+            if (ms / reps < best) {
+                best = ms / reps;
+                bb = bx;
+                br = r;
+            }
+        }
+        if (rc != LB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rc2 = lb_set_tile(h, rc == LB_OK ? bb : old_bx, rc == LB_OK ? br : old_rows);
+    if (rc != LB_OK) return rc;
+    if (rc2 != LB_OK) return rc2;
+    if (block_x) *block_x = bb;
+    if (rows) *rows = br;
+    if (best_ms) *best_ms = best;
+    return LB_OK;
+}
+
+long long lb_step_count(const lb_handle* h) { return h ? h->steps : -1; }
+
+int lb_sync(lb_handle* h)
+{
+    if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+long long lb_launch_count(const lb_handle* h) { return h ? h->launches : -1; }
+
+const char* lb_error_string(int code)
+{
+    switch (code) {
+        case LB_OK: return "ok";
+        case LB_ERR_INVALID_ARG: return "invalid argument";
+        case LB_ERR_CUDA: return "CUDA error";
+        case LB_ERR_NONFINITE: return "non-finite state";
+        case LB_ERR_TIMEOUT: return "device wait timed out";
+        case LB_ERR_NO_INTERFACE: return "no interface to fit";
+        case LB_ERR_CAPACITY: return "interface buffer too small";
+        default: return "unknown error";
+    }
+}
+
+const char* lb_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Internal host/device interface of the library (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lbfe {
+
+// One domain as the kernels see it.  Populations live in two ping-pong
+// buffers; buffer b holds f at f[b] and g at g[b], each 9 planes of
+// `plane` elements (pitch * ny, x fastest, pitch >= nx).
+struct DomDesc {
+    void* f[2];
+    void* g[2];
+    long long plane;   // elements per population plane
+    int nx, ny, pitch;
+    int walls;         // 1: bounce-back walls below row 0 and above row ny-1
+    int step2;         // zero equilibrium velocity on wall rows (Sec. V, Step 2)
+    int pad_;
+    double a, kappa, gamma;   // free energy and mobility parameters
+    double omega_phi;         // 1 / tau_phi
+    double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)
+    double h_bot, h_top;      // wetting gradients
+};
+
+// A rectangular piece of one domain processed by one CTA: columns
+// [x0, x0 + blockDim.x) and rows [y0, y0 + rows).
+struct WorkItem {
+    int dom, x0, y0, rows;
+};
+
+// Per-domain reduction result written by the moments kernels.
+struct StatsOut {
+    double mass, order, mom_x, mom_y, max_u;
+    double nonfinite;
+};
+
+constexpr int kStatsFields = 6;
+
+// Launchers implemented in the .cu files.  All return a cudaError_t value
+// cast to int (0 = success) and enqueue on `stream`.
+int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
+                const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x,
+                int rows, int grid_persistent, void* stream);
+
+int launch_init_phi_drop(int precision, const DomDesc& d, double* phi0, double R, double cx,
+                         double cy, void* stream);
+int launch_init_phi_random(int precision, const DomDesc& d, double* phi0, double amp,
+                           unsigned long long seed, void* stream);
+int launch_init_eq(int precision, const DomDesc& d, const double* phi0, int parity,
+                   void* stream);
+int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nrows,
+                   double* rho, double* phi, double* ux, double* uy, long long ld,
+                   double* partials, int max_partials, StatsOut* out, void* stream);
+int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, int* count,
+                     int cap, void* stream);
+
+int max_partials_needed(int nx, int ny);
+
+}  // namespace lbfe

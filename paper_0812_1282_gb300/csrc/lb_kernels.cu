@@ -1,0 +1,405 @@
+// Kernels and their launchers: fused step (single domain and batched work
+// list), initial state, moments / diagnostics and interface points.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lb_internal.h"
+#include "lb_node.cuh"
+#include "lb_step.cuh"
+
+namespace lbfe {
+
+// ------------------------------------------------------------------ step
+template <typename Real, bool MRT>
+__global__ void __launch_bounds__(512) step_single_kernel(DomDesc D, int parity, int rows)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* ring = reinterpret_cast<Real*>(smem_raw);
+    const int x0 = blockIdx.x * blockDim.x;
+    const int y0 = blockIdx.y * rows;
+    process_tile<Real, MRT>(D, parity, x0, y0, rows, ring);
+}
+
+// Persistent form: a fixed grid walks a precomputed list of tiles of many
+// domains (grid-stride, static order).
+template <typename Real, bool MRT>
+__global__ void __launch_bounds__(512) step_batch_kernel(const DomDesc* __restrict__ descs,
+                                                         const WorkItem* __restrict__ items,
+                                                         int n_items, int parity)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* ring = reinterpret_cast<Real*>(smem_raw);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const DomDesc D = descs[w.dom];
+        process_tile<Real, MRT>(D, parity, w.x0, w.y0, w.rows, ring);
+    }
+}
+
+template <typename Real, bool MRT>
+static cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                                 int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
+                                 cudaStream_t s)
+{
+    const size_t smem = 4 * size_t(bx + 2) * sizeof(Real);
+    if (n_dom == 1 && d_items == nullptr) {
+        dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
+        step_single_kernel<Real, MRT><<<grid, bx, smem, s>>>(d, parity, rows);
+    } else {
+        const int grid = grid_p > 0 ? grid_p : n_items;
+        step_batch_kernel<Real, MRT><<<grid, bx, smem, s>>>(d_descs, d_items, n_items, parity);
+    }
+    return cudaGetLastError();
+}
+
+int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
+                const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x, int rows,
+                int grid_persistent, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (precision == 0) {
+        e = coll ? launch_step_t<float, true>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
+                                              rows, grid_persistent, s)
+                 : launch_step_t<float, false>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
+                                               rows, grid_persistent, s);
+    } else {
+        e = coll ? launch_step_t<double, true>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
+                                               rows, grid_persistent, s)
+                 : launch_step_t<double, false>(d, d_descs, d_items, n_items, n_dom, parity,
+                                                block_x, rows, grid_persistent, s);
+    }
+    return static_cast<int>(e);
+}
+
+// ------------------------------------------------------------ init phi0
+// phi0 is a double field with the domain's pitch (it lives in the idle
+// ping-pong buffer during initialisation).
+__global__ void init_phi_drop_kernel(int nx, int ny, int pitch, double* phi0, double R, double cx,
+                                     double cy, double ell)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = int(k / nx), x = int(k - (long long)y * nx);
+        const double ddx = x - cx, ddy = y - cy;
+        phi0[(long long)y * pitch + x] = tanh((R - sqrt(ddx * ddx + ddy * ddy)) / ell);
+    }
+}
+
+// SplitMix64 used as a counter-based generator (Steele, Lea & Flood 2014):
+// draw k of the stream seeded with s is mix(s + (k + 1) * golden gamma).
+__device__ __forceinline__ unsigned long long splitmix64_draw(unsigned long long seed,
+                                                              unsigned long long k)
+{
+    unsigned long long z = seed + (k + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void init_phi_random_kernel(int nx, int ny, int pitch, double* phi0, double amp,
+                                       unsigned long long seed)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = int(k / nx), x = int(k - (long long)y * nx);
+        const double u = double(splitmix64_draw(seed, (unsigned long long)k) >> 11) * 0x1.0p-53;
+        phi0[(long long)y * pitch + x] = amp * (2.0 * u - 1.0);
+    }
+}
+
+static int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 16) g = 152LL * 16;
+    if (g < 1) g = 1;
+    return int(g);
+}
+
+int launch_init_phi_drop(int, const DomDesc& d, double* phi0, double R, double cx, double cy,
+                         void* stream)
+{
+    const double ell = sqrt(2.0 * d.kappa / d.a);
+    const long long n = (long long)d.nx * d.ny;
+    init_phi_drop_kernel<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d.nx, d.ny, d.pitch, phi0, R, cx, cy, ell);
+    return static_cast<int>(cudaGetLastError());
+}
+
+int launch_init_phi_random(int, const DomDesc& d, double* phi0, double amp,
+                           unsigned long long seed, void* stream)
+{
+    const long long n = (long long)d.nx * d.ny;
+    init_phi_random_kernel<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d.nx, d.ny, d.pitch, phi0, amp, seed);
+    return static_cast<int>(cudaGetLastError());
+}
+
+// f = f^eq, g = g^eq of (rho = 1, u = 0, phi0) with the stencils of Eq.
+// (best) and the wetting ghost rows; computed in FP64, stored as Real.
+template <typename Real>
+__global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int parity)
+{
+    Real* fd = static_cast<Real*>((parity ? D.f[1] : D.f[0]));
+    Real* gd = static_cast<Real*>((parity ? D.g[1] : D.g[0]));
+    const int nx = D.nx, ny = D.ny, pitch = D.pitch;
+    const long long P = D.plane;
+    NodeParams<double> prm;
+    prm.a = D.a;
+    prm.kappa = D.kappa;
+    prm.gamma = D.gamma;
+    prm.omega_phi = D.omega_phi;
+    prm.tau_c0 = D.tau_c0;
+    prm.tau_c1 = D.tau_c1;
+    prm.h_bot = D.h_bot;
+    prm.h_top = D.h_top;
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = int(k / nx), x = int(k - (long long)y * nx);
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
+        // phi in rows y-1, y, y+1 at columns xm, x, xp
+        double v[3][3];
+        for (int r = 0; r < 3; ++r) {
+            const int yy = y + r - 1;
+            const int cols[3] = {xm, x, xp};
+            for (int c = 0; c < 3; ++c) {
+                double val;
+                if (D.walls && yy < 0)
+                    val = phi0[(long long)1 * pitch + cols[c]] - 2.0 * D.h_bot;
+                else if (D.walls && yy >= ny)
+                    val = phi0[(long long)(ny - 2) * pitch + cols[c]] - 2.0 * D.h_top;
+                else {
+                    const int yw = yy < 0 ? ny - 1 : (yy >= ny ? 0 : yy);
+                    val = phi0[(long long)yw * pitch + cols[c]];
+                }
+                v[r][c] = val;
+            }
+        }
+        double dx, dy, lap;
+        stencils<double>(v[1][1], v[1][2], v[1][0], v[2][1], v[0][1], v[2][2], v[2][0], v[0][2],
+                         v[0][0], dx, dy, lap);
+        double fe[9], ge[9];
+        const double phi = v[1][1];
+        equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge);
+        fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
+        ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
+        const long long o = (long long)y * pitch + x;
+        for (int i = 0; i < 9; ++i) {
+            fd[i * P + o] = Real(fe[i]);
+            gd[i * P + o] = Real(ge[i]);
+        }
+    }
+}
+
+int launch_init_eq(int precision, const DomDesc& d, const double* phi0, int parity, void* stream)
+{
+    const long long n = (long long)d.nx * d.ny;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 0)
+        init_eq_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(d, phi0, parity);
+    else
+        init_eq_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d, phi0, parity);
+    return static_cast<int>(cudaGetLastError());
+}
+
+// ------------------------------------------------------------- moments
+// Moments of the stored populations (Eq. moments) on rows
+// [row0, row0 + nrows): optional FP64 field outputs (leading dimension ld,
+// row-relative), and per-block partial sums for the diagnostics.
+// Reductions: fixed grid, per-thread serial accumulation, warp shuffles,
+// one partial per block, then a single-block pass in fixed order, so the
+// result is deterministic.
+constexpr int kMomBlock = 256;
+constexpr int kMaxMomBlocks = 1024;
+
+int max_partials_needed(int, int) { return kMaxMomBlocks; }
+
+__device__ __forceinline__ void warp_reduce(double (&v)[kStatsFields])
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < kStatsFields; ++k) {
+            const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
+            v[k] = (k == 4) ? fmax(v[k], o) : v[k] + o;
+        }
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parity, int row0,
+                                                            int nrows, double* rho, double* phi,
+                                                            double* ux, double* uy, long long ld,
+                                                            double* partials)
+{
+    const Real* fs = static_cast<const Real*>((parity ? D.f[1] : D.f[0]));
+    const Real* gs = static_cast<const Real*>((parity ? D.g[1] : D.g[0]));
+    const long long P = D.plane;
+    const int nx = D.nx, pitch = D.pitch;
+    const long long n = (long long)nx * nrows;
+    double acc[kStatsFields] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int yr = int(k / nx), x = int(k - (long long)yr * nx);
+        const long long o = (long long)(row0 + yr) * pitch + x;
+        double f[9], g[9];
+        for (int i = 0; i < 9; ++i) {
+            f[i] = double(fs[i * P + o]);
+            g[i] = double(gs[i * P + o]);
+        }
+        const double drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+        const double jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const double jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
+        const double ph = phi_sum<double>(g);
+        const double r = 1.0 + drho;
+        const double vx = jx / r, vy = jy / r;
+        const long long q = (long long)yr * ld + x;
+        if (rho) rho[q] = r;
+        if (phi) phi[q] = ph;
+        if (ux) ux[q] = vx;
+        if (uy) uy[q] = vy;
+        const double um = sqrt(vx * vx + vy * vy);
+        const bool finite = isfinite(r) && isfinite(ph) && isfinite(um);
+        acc[0] += r;
+        acc[1] += ph;
+        acc[2] += jx;
+        acc[3] += jy;
+        acc[4] = finite ? fmax(acc[4], um) : acc[4];
+        acc[5] += finite ? 0.0 : 1.0;
+    }
+    if (partials == nullptr) return;
+    warp_reduce(acc);
+    __shared__ double red[kMomBlock / 32][kStatsFields];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < kStatsFields; ++k) red[wid][k] = acc[k];
+    __syncthreads();
+    if (wid == 0) {
+        double v[kStatsFields];
+        for (int k = 0; k < kStatsFields; ++k)
+            v[k] = lane < (kMomBlock / 32) ? red[lane][k] : (k == 4 ? 0.0 : 0.0);
+        warp_reduce(v);
+        if (lane == 0)
+            for (int k = 0; k < kStatsFields; ++k) partials[blockIdx.x * kStatsFields + k] = v[k];
+    }
+}
+
+__global__ void finalize_stats_kernel(const double* __restrict__ partials, int nblocks,
+                                      StatsOut* out)
+{
+    double acc[kStatsFields] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < kStatsFields; ++k) {
+            const double v = partials[b * kStatsFields + k];
+            acc[k] = (k == 4) ? fmax(acc[k], v) : acc[k] + v;
+        }
+    warp_reduce(acc);
+    __shared__ double red[32][kStatsFields];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < kStatsFields; ++k) red[wid][k] = acc[k];
+    __syncthreads();
+    if (wid == 0) {
+        double v[kStatsFields];
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < kStatsFields; ++k) v[k] = lane < nw ? red[lane][k] : 0.0;
+        warp_reduce(v);
+        if (lane == 0) {
+            out->mass = v[0];
+            out->order = v[1];
+            out->mom_x = v[2];
+            out->mom_y = v[3];
+            out->max_u = v[4];
+            out->nonfinite = v[5];
+        }
+    }
+}
+
+int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nrows, double* rho,
+                   double* phi, double* ux, double* uy, long long ld, double* partials,
+                   int max_partials, StatsOut* out, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)d.nx * nrows;
+    long long g = (n + kMomBlock - 1) / kMomBlock;
+    if (g > kMaxMomBlocks) g = kMaxMomBlocks;
+    if (out && g > max_partials) g = max_partials;
+    if (g < 1) g = 1;
+    const int grid = int(g);
+    double* part = out ? partials : nullptr;
+    if (precision == 0)
+        moments_kernel<float><<<grid, kMomBlock, 0, s>>>(d, parity, row0, nrows, rho, phi, ux, uy,
+                                                         ld, part);
+    else
+        moments_kernel<double><<<grid, kMomBlock, 0, s>>>(d, parity, row0, nrows, rho, phi, ux,
+                                                          uy, ld, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || out == nullptr) return static_cast<int>(e);
+    finalize_stats_kernel<<<1, 256, 0, s>>>(partials, grid, out);
+    return static_cast<int>(cudaGetLastError());
+}
+
+// ----------------------------------------------------- interface points
+// phi = 0 crossings on horizontal (periodic) and vertical links whose ends
+// have phi > 0 and phi < 0, by linear interpolation (Sec. IV).  Points are
+// appended in arbitrary order; the host sorts them.
+template <typename Real>
+__device__ __forceinline__ double phi_at_node(const Real* g, long long P, long long o)
+{
+    double v[9];
+    for (int i = 0; i < 9; ++i) v[i] = double(g[i * P + o]);
+    return phi_sum<double>(v);
+}
+
+template <typename Real>
+__global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count, int cap)
+{
+    const Real* gs = static_cast<const Real*>((parity ? D.g[1] : D.g[0]));
+    const long long P = D.plane;
+    const int nx = D.nx, ny = D.ny, pitch = D.pitch;
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = int(k / nx), x = int(k - (long long)y * nx);
+        const double a = phi_at_node(gs, P, (long long)y * pitch + x);
+        const int xp = x + 1 == nx ? 0 : x + 1;
+        const double b = phi_at_node(gs, P, (long long)y * pitch + xp);
+        if ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0)) {
+            const int idx = atomicAdd(count, 1);
+            if (idx < cap) {
+                pts[2 * idx] = x + a / (a - b);
+                pts[2 * idx + 1] = double(y);
+            }
+        }
+        if (y + 1 < ny) {
+            const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x);
+            if ((a > 0.0 && c < 0.0) || (a < 0.0 && c > 0.0)) {
+                const int idx = atomicAdd(count, 1);
+                if (idx < cap) {
+                    pts[2 * idx] = double(x);
+                    pts[2 * idx + 1] = y + a / (a - c);
+                }
+            }
+        }
+    }
+}
+
+int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, int* count, int cap,
+                     void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    const long long n = (long long)d.nx * d.ny;
+    if (precision == 0)
+        crossings_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(d, parity, pts, count, cap);
+    else
+        crossings_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d, parity, pts, count, cap);
+    return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace lbfe

@@ -1,0 +1,163 @@
+// Per-node arithmetic of the binary-fluid lattice Boltzmann step, shared by
+// the step, initialisation and diagnostic kernels (device code only).
+//
+// Storage is in deviation form for f: the stored value is f_i - t_i with
+// t = (4/9, 1/9 x4, 1/36 x4) the rest-state weights (rho = 1, u = 0), so
+// that rho - 1 and rho*u come out of sums of small numbers.  g is stored
+// as is (its rest state is g_0 = phi, g_i = 0).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbfe {
+
+template <typename Real>
+struct NodeParams {
+    Real a, kappa, gamma, omega_phi, tau_c0, tau_c1, h_bot, h_top;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real rcp_rn(Real x);
+template <>
+__device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
+
+// phi = sum_i g_i (Eq. moments), always in this order so that every thread
+// that evaluates phi at a node gets the same bits.
+template <typename Real>
+__device__ __forceinline__ Real phi_sum(const Real (&g)[9])
+{
+    return (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
+}
+
+// Eq. (best): isotropic gradient (1/12 [-1 0 1; -4 0 4; -1 0 1] and its
+// transpose) and nine-point Laplacian (1/6 [1 4 1; 4 -20 4; 1 4 1]).
+template <typename Real>
+__device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s, Real ne, Real nw,
+                                         Real se, Real sw, Real& dx, Real& dy, Real& lap)
+{
+    const Real c12 = Real(1) / Real(12), c6 = Real(1) / Real(6);
+    dx = (Real(4) * (e - w) + (ne - nw) + (se - sw)) * c12;
+    dy = (Real(4) * (n - s) + (ne - se) + (nw - sw)) * c12;
+    lap = (Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - Real(20) * c) * c6;
+}
+
+// Equilibria of Appendix A (Eq. equilibrium) for i = 1..8, f in deviation
+// form: fe[i] = f^eq_i - t_i, using w_i p0 = t_i rho + w_i a(-phi^2/2 +
+// 3 phi^4/4) (Eq. p0, c = 1).  (jxe, jye) = rho u_eq and (uxe, uye) = u_eq
+// are the equilibrium momentum / velocity (zero at Step-2 nodes).
+// Returns mu (Eq. chempot) for the caller's diagnostics.
+template <typename Real>
+__device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
+                                           Real jxe, Real jye, Real uxe, Real uye, Real dx,
+                                           Real dy, Real lap, Real (&fe)[9], Real (&ge)[9])
+{
+    const Real c3 = Real(1) / Real(3), c6 = Real(1) / Real(6), c12 = Real(1) / Real(12),
+               c24 = Real(1) / Real(24);
+    const Real phi2 = phi * phi;
+    // isotropic part: w_i [p0 - kappa phi lap] minus the rest weight
+    const Real A = drho * c3 + P.a * phi2 * (Real(0.75) * phi2 - Real(0.5)) - P.kappa * phi * lap;
+    // rho u_a u_b
+    const Real rxx = jxe * uxe, ryy = jye * uye, rxy = jxe * uye;
+    const Real ruu = rxx + ryy;
+    // kappa d_a phi d_b phi with the w^xx, w^yy, w^xy tables
+    const Real kxx = P.kappa * dx * dx, kyy = P.kappa * dy * dy, kxy = P.kappa * dx * dy;
+    const Real kd = -(kxx + kyy) * c24;
+    const Real bx = c3 * (A + Real(1.5) * rxx - Real(0.5) * ruu) + c3 * kxx - c6 * kyy;
+    const Real by = c3 * (A + Real(1.5) * ryy - Real(0.5) * ruu) - c6 * kxx + c3 * kyy;
+    const Real bd = c12 * (A + ruu + Real(3) * rxy) + kd + Real(0.25) * kxy;  // e = +-(1,1)
+    const Real ba = c12 * (A + ruu - Real(3) * rxy) + kd - Real(0.25) * kxy;  // e = +-(-1,1)
+    fe[1] = bx + c3 * jxe;
+    fe[2] = bx - c3 * jxe;
+    fe[3] = by + c3 * jye;
+    fe[4] = by - c3 * jye;
+    fe[5] = bd + c12 * (jxe + jye);
+    fe[6] = bd - c12 * (jxe + jye);
+    fe[7] = ba + c12 * (jye - jxe);
+    fe[8] = ba - c12 * (jye - jxe);
+    // g: w_i [Gamma mu + phi e.u + 3/2 phi (e.u e.u - u.u/3)]
+    const Real mu = P.a * (phi2 * phi - phi) - P.kappa * lap;
+    const Real G = P.gamma * mu;
+    const Real pux = phi * uxe, puy = phi * uye;
+    const Real pxx = pux * uxe, pyy = puy * uye, pxy = pux * uye;
+    const Real puu = pxx + pyy;
+    const Real gx = c3 * (G + Real(1.5) * pxx - Real(0.5) * puu);
+    const Real gy = c3 * (G + Real(1.5) * pyy - Real(0.5) * puu);
+    const Real gd = c12 * (G + puu + Real(3) * pxy);
+    const Real ga = c12 * (G + puu - Real(3) * pxy);
+    ge[1] = gx + c3 * pux;
+    ge[2] = gx - c3 * pux;
+    ge[3] = gy + c3 * puy;
+    ge[4] = gy - c3 * puy;
+    ge[5] = gd + c12 * (pux + puy);
+    ge[6] = gd - c12 * (pux + puy);
+    ge[7] = ga + c12 * (puy - pux);
+    ge[8] = ga - c12 * (puy - pux);
+}
+
+// One node of Steps 1-3 (Sec. V): moments of the pulled populations f, g,
+// thermodynamics from the phi stencil values, Step 2, equilibria and BGK
+// or MRT collision.  fo, go receive the post-collision populations (f in
+// deviation form).  f'_0 and g'_0 follow from conservation of rho and phi,
+// which both collisions satisfy exactly (Eq. feq0, S_0 = 0).
+//
+// MRT: f' = f - M^-1 S M (f - f^eq) with S = diag(0,1,1,0,1,0,1,w,w) is
+// evaluated as f' = f^eq + M^-1 (I - S) M (f - f^eq): only the momentum
+// rows (rate 0; non-zero only where Step 2 zeroes u_eq) and the two stress
+// rows (rate w) survive, so
+//   f'_i = f^eq_i + M_3i dj_x/6 + M_5i dj_y/6 + (1-w)(M_7i m_7 + M_8i m_8)/4,
+// with m_7 = d1+d2-d3-d4, m_8 = d5+d6-d7-d8, d = f - f^eq.
+template <typename Real, bool MRT>
+__device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&f)[9],
+                                        const Real (&g)[9], Real phi, Real dx, Real dy, Real lap,
+                                        bool step2, Real (&fo)[9], Real (&go)[9])
+{
+    // Step 1 (Eq. moments); t_i e_i sums to zero, so deviations give j directly
+    const Real drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+    const Real jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const Real jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
+    const Real rho = Real(1) + drho;
+    const Real irho = rcp_rn(rho);
+    // Eq. (tau)
+    const Real omega = rcp_rn(P.tau_c0 + P.tau_c1 * phi);
+    // Step 2
+    Real jxe = jx, jye = jy, uxe = jx * irho, uye = jy * irho;
+    if (step2) {
+        jxe = Real(0);
+        jye = Real(0);
+        uxe = Real(0);
+        uye = Real(0);
+    }
+    Real fe[9], ge[9];
+    equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, ge);
+    // Step 3
+    if (MRT) {
+        const Real m7 = ((f[1] - fe[1]) + (f[2] - fe[2])) - ((f[3] - fe[3]) + (f[4] - fe[4]));
+        const Real m8 = ((f[5] - fe[5]) + (f[6] - fe[6])) - ((f[7] - fe[7]) + (f[8] - fe[8]));
+        const Real s = (Real(1) - omega) * Real(0.25);
+        const Real c7 = s * m7, c8 = s * m8;
+        const Real c6 = Real(1) / Real(6);
+        const Real cx = (jx - jxe) * c6, cy = (jy - jye) * c6;
+        fo[1] = fe[1] + c7 + cx;
+        fo[2] = fe[2] + c7 - cx;
+        fo[3] = fe[3] - c7 + cy;
+        fo[4] = fe[4] - c7 - cy;
+        fo[5] = fe[5] + c8 + (cx + cy);
+        fo[6] = fe[6] + c8 - (cx + cy);
+        fo[7] = fe[7] - c8 + (cy - cx);
+        fo[8] = fe[8] - c8 - (cy - cx);
+    } else {
+        const Real k = Real(1) - omega;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fo[i] = fe[i] + k * (f[i] - fe[i]);
+    }
+    fo[0] = drho - ((((fo[1] + fo[2]) + (fo[3] + fo[4])) + ((fo[5] + fo[6]) + (fo[7] + fo[8]))));
+    // Eq. (gevo)
+    const Real kg = Real(1) - P.omega_phi;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) go[i] = ge[i] + kg * (g[i] - ge[i]);
+    go[0] = phi - ((((go[1] + go[2]) + (go[3] + go[4])) + ((go[5] + go[6]) + (go[7] + go[8]))));
+}
+
+}  // namespace lbfe

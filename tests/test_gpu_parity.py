@@ -1,0 +1,370 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 GPU vs oracle 1e-12 absolute in phi and u (rounding
+order only); FP32 GPU (deviation storage) vs the FP64 oracle 1e-5 in phi
+after 1000 steps, contact angle within 0.5 degrees.  Integer-like results
+(tile-shape and batch independence, checkpoint resume) are bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lbinputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0812_1282_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def make_pair(lbf, orc, nx, ny, precision="fp64", **kw):
+    gp = lbf.params(precision=precision, **kw)
+    op = orc.params(**kw)
+    return lbf.Lattice(gp, nx, ny), orc.OracleLattice(op, nx, ny)
+
+
+def max_diff(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max())
+
+
+# ------------------------------------------------------------ init
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 1e-7)])
+@pytest.mark.parametrize("walls", [True, False])
+def test_init_drop_matches_oracle(lbf, orc, precision, tol, walls):
+    kw = dict(h_bottom=orc.wetting_h(60.0), h_top=0.1, walls=walls)
+    sim, ref = make_pair(lbf, orc, 67, 29, precision, **kw)
+    sim.init_drop(15.0, 33.0, -0.5)
+    ref.init_drop(15.0, 33.0, -0.5)
+    f, g = sim.populations()
+    assert max_diff(f, ref.f) <= tol
+    assert max_diff(g, ref.g) <= tol
+
+
+def test_init_random_matches_oracle(lbf, orc):
+    sim, ref = make_pair(lbf, orc, 45, 19, "fp64", collision="mrt", tau_alpha=1.5, tau_beta=0.6)
+    sim.init_random(0.1, 12345)
+    ref.init_random(0.1, 12345)
+    f, g = sim.populations()
+    assert max_diff(f, ref.f) <= 1e-15
+    assert max_diff(g, ref.g) <= 1e-15
+
+
+# --------------------------------------------------- FP64 full runs
+def test_fp64_bgk_drop_100x50_2000_steps(lbf, orc):
+    """Plain BGK, FP64, 100x50 drop of radius 20 on a neutral wall, tau = 1,
+    2000 steps: phi and u within 1e-12 of the oracle, mass and order
+    parameter conserved to 1e-12, angle within 0.5 degrees of the oracle."""
+    c = lbinputs.DROP_100x50
+    sim, ref = make_pair(lbf, orc, c["nx"], c["ny"], "fp64", **c["params"])
+    sim.init_drop(c["R"], c["cx"], c["cy"])
+    ref.init_drop(c["R"], c["cx"], c["cy"])
+    s0 = sim.stats()
+    sim.step(c["steps"])
+    ref.step(c["steps"])
+    rho, phi, ux, uy, st = sim.moments()
+    rrho, rphi, rux, ruy = ref.moments()
+    assert max_diff(phi, rphi) <= 1e-12
+    assert max_diff(ux, rux) <= 1e-12 and max_diff(uy, ruy) <= 1e-12
+    assert max_diff(rho, rrho) <= 1e-12
+    assert abs(st["mass"] - s0["mass"]) <= 1e-12 * s0["mass"]
+    assert abs(st["order"] - s0["order"]) <= 1e-12 * s0["mass"]
+    th = sim.contact_angle()[0]
+    th_ref = orc.contact_angle(rphi)[0]
+    assert th == pytest.approx(th_ref, abs=1e-6)
+    assert st["step"] == c["steps"]
+
+
+@pytest.mark.parametrize("coll,step2", [("mrt", True), ("mrt", False), ("bgk", True)])
+def test_fp64_viscosity_ratio_wetting(lbf, orc, coll, step2):
+    kw = dict(collision=coll, zero_u_at_walls=step2, tau_alpha=3.0, tau_beta=0.7,
+              h_bottom=orc.wetting_h(60.0), h_top=orc.wetting_h(110.0), gamma_mob=0.5)
+    sim, ref = make_pair(lbf, orc, 96, 40, "fp64", **kw)
+    sim.init_drop(18.0, 48.0, -0.5)
+    ref.init_drop(18.0, 48.0, -0.5)
+    sim.step(1000)
+    ref.step(1000)
+    f, g = sim.populations()
+    assert max_diff(f, ref.f) <= 1e-12
+    assert max_diff(g, ref.g) <= 1e-12
+
+
+def _random_flow_state(orc, p, nx, ny, seed):
+    """Populations = equilibria of smooth random (rho, u, phi) fields with
+    matching stencils, plus a small seeded non-equilibrium part."""
+    rho = 1.0 + lbinputs.smooth_random_field(nx, ny, 0.02, seed)
+    ux = lbinputs.smooth_random_field(nx, ny, 0.05, seed + 1)
+    uy = lbinputs.smooth_random_field(nx, ny, 0.05, seed + 2)
+    phi = lbinputs.smooth_random_field(nx, ny, 1.0, seed + 3)
+    dx, dy, lap = orc.phi_derivatives(p, phi)
+    f = np.zeros((9, ny, nx))
+    g = np.zeros((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            fe, ge = orc.node_equilibrium(p, rho[y, x], phi[y, x], ux[y, x], uy[y, x],
+                                          dx[y, x], dy[y, x], lap[y, x])
+            f[:, y, x] = fe
+            g[:, y, x] = ge
+    noise = lbinputs.random_field(nx * 9, ny * 2, 1e-4, seed + 4).reshape(2, 9, ny, nx)
+    return f + noise[0], g + noise[1]
+
+
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+@pytest.mark.parametrize("walls", [True, False])
+def test_fp64_random_flow_states(lbf, orc, coll, walls):
+    """Arbitrary states with flow (every velocity term of the equilibria,
+    Step 2 with u != 0, bounce-back of non-equilibrium populations): a few
+    steps from the same populations agree to 1e-13."""
+    nx, ny = 41, 23
+    kw = dict(collision=coll, tau_alpha=1.7, tau_beta=0.65, tau_phi=0.9, walls=walls,
+              h_bottom=0.13, h_top=-0.21, gamma_mob=0.3)
+    sim, ref = make_pair(lbf, orc, nx, ny, "fp64", **kw)
+    f, g = _random_flow_state(orc, ref.p, nx, ny, 7)
+    ref.f[:] = f
+    ref.g[:] = g
+    sim.set_populations(f, g)
+    for n in (1, 2, 5):
+        sim.step(n)
+        ref.step(n)
+        fs, gs = sim.populations()
+        assert max_diff(fs, ref.f) <= 1e-13
+        assert max_diff(gs, ref.g) <= 1e-13
+
+
+# --------------------------------------- ragged sizes and tile shapes
+@pytest.mark.parametrize("nx,ny,walls", [(3, 3, True), (37, 5, True), (129, 67, False),
+                                         (130, 66, True), (33, 4, False)])
+def test_ragged_sizes_and_tile_independence(lbf, orc, nx, ny, walls):
+    """Results do not depend on the launch shape (bit-exact) and match the
+    oracle on lattices that leave ragged tiles in x and y."""
+    kw = dict(collision="mrt", tau_alpha=1.5, tau_beta=0.6, walls=walls,
+              h_bottom=orc.wetting_h(70.0), h_top=orc.wetting_h(100.0))
+    phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 5)
+    ref = orc.OracleLattice(orc.params(**kw), nx, ny)
+    ref.init_phi(phi0)
+    ref.step(40)
+    outs = []
+    for bx, rows in [(32, 1), (64, 3), (128, 7), (512, 128), (96, 2)]:
+        sim = lbf.Lattice(lbf.params(precision="fp64", **kw), nx, ny)
+        sim.set_tile(bx, rows)
+        sim.init_phi(phi0)
+        sim.step(40)
+        f, g = sim.populations()
+        outs.append((f, g))
+        sim.close()
+    for f, g in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and np.array_equal(g, outs[0][1])
+    assert max_diff(outs[0][0], ref.f) <= 1e-12
+    assert max_diff(outs[0][1], ref.g) <= 1e-12
+
+
+def test_fp32_tile_independence(lbf):
+    nx, ny = 200, 100
+    kw = dict(collision="mrt", tau_alpha=1.5, tau_beta=0.6, h_bottom=lbf.lb_wetting_h(60.0),
+              precision="fp32")
+    outs = []
+    for bx, rows in [(128, 32), (64, 5), (256, 100)]:
+        sim = lbf.Lattice(lbf.params(**kw), nx, ny)
+        sim.set_tile(bx, rows)
+        sim.init_drop(40.0, 100.0, -0.5)
+        sim.step(300)
+        outs.append(sim.save_state())
+        sim.close()
+    assert outs[0] == outs[1] == outs[2]
+
+
+# ---------------------------------------------------------- FP32
+@pytest.mark.parametrize("coll,taus", [("bgk", (1.0, 1.0)), ("mrt", (1.5, 0.6)),
+                                       ("bgk", (1.5, 0.6))])
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_fp32_phi_within_1e5_after_1000_steps(lbf, orc, coll, taus, theta):
+    c = lbinputs.SWEEP_200x100
+    kw = dict(lbinputs.BASE, collision=coll, tau_alpha=taus[0], tau_beta=taus[1],
+              h_bottom=orc.wetting_h(theta), h_top=0.0)
+    sim, ref = make_pair(lbf, orc, c["nx"], c["ny"], "fp32", **kw)
+    sim.init_drop(c["R"], c["cx"], c["cy"])
+    ref.init_drop(c["R"], c["cx"], c["cy"])
+    sim.step(1000)
+    ref.step(1000)
+    _, phi, ux, uy, _ = sim.moments()
+    _, rphi, rux, ruy = ref.moments()
+    assert max_diff(phi, rphi) <= 1e-5
+    assert max_diff(ux, rux) <= 1e-5 and max_diff(uy, ruy) <= 1e-5
+
+
+def test_fp32_spinodal_subrun_512(lbf, orc):
+    """512x512 cut of the 8192^2 roofline workload (same generator, same
+    parameters, MRT), 200 steps in FP32 against the FP64 oracle."""
+    c = lbinputs.SPINODAL_8192
+    n = c["sub"]
+    kw = dict(c["params"])
+    sim, ref = make_pair(lbf, orc, n, n, "fp32", **kw)
+    sim.init_random(c["amp"], c["seed"])
+    ref.init_random(c["amp"], c["seed"])
+    sim.step(200)
+    ref.step(200)
+    _, phi, _, _, _ = sim.moments()
+    _, rphi, _, _ = ref.moments()
+    assert max_diff(phi, rphi) <= 1e-5
+
+
+# ------------------------------------------- diagnostics and angle
+def test_stats_match_fields(lbf, orc):
+    sim, _ = make_pair(lbf, orc, 77, 31, "fp64", collision="mrt", tau_alpha=1.5, tau_beta=0.6,
+                       h_bottom=0.2)
+    sim.init_drop(14.0, 38.0, -0.5)
+    sim.step(123)
+    rho, phi, ux, uy, st = sim.moments()
+    assert st["mass"] == pytest.approx(rho.sum(), rel=1e-13)
+    assert st["order"] == pytest.approx(phi.sum(), abs=1e-10)
+    assert st["mom_x"] == pytest.approx((rho * ux).sum(), abs=1e-12)
+    assert st["mom_y"] == pytest.approx((rho * uy).sum(), abs=1e-12)
+    assert st["max_u"] == pytest.approx(np.hypot(ux, uy).max(), rel=1e-12)
+    assert st["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("theta", [45.0, 90.0, 135.0])
+def test_contact_angle_matches_oracle_fit(lbf, orc, theta):
+    """lb_contact_angle (device crossings + host fit) against the oracle's
+    numpy pipeline on the same FP64 state."""
+    kw = dict(collision="mrt", tau_alpha=1.0, tau_beta=1.0, h_bottom=orc.wetting_h(theta))
+    sim, ref = make_pair(lbf, orc, 120, 60, "fp64", **kw)
+    sim.init_drop(25.0, 60.0, -0.5)
+    ref.init_drop(25.0, 60.0, -0.5)
+    sim.step(1500)
+    ref.step(1500)
+    th, R, xc, yc = sim.contact_angle()
+    _, rphi, _, _ = ref.moments()
+    rth, rR, rxc, ryc = orc.contact_angle(rphi)
+    assert th == pytest.approx(rth, abs=1e-6)
+    assert R == pytest.approx(rR, abs=1e-6)
+
+
+def test_contact_angle_without_interface_is_an_error(lbf):
+    sim = lbf.Lattice(lbf.params(), 32, 16)
+    sim.init_phi(np.ones((16, 32)))
+    with pytest.raises(lbf.LBError) as e:
+        sim.contact_angle()
+    assert e.value.code == lbf.LB_ERR_NO_INTERFACE
+
+
+# ----------------------------------------------- batching, checkpoint
+def test_batch_is_bitwise_equal_to_single_domains(lbf):
+    specs = lbinputs.batch_specs(6, seed=2026, lo=24, hi=90)
+    plist, nxs, nys = [], [], []
+    for s in specs:
+        plist.append(lbf.params(collision="mrt", precision="fp32", tau_alpha=s["tau_alpha"],
+                                tau_beta=s["tau_beta"], h_bottom=lbf.lb_wetting_h(s["theta"])))
+        nxs.append(s["nx"])
+        nys.append(s["ny"])
+    batch = lbf.Batch(plist, nxs, nys)
+    for d, s in enumerate(specs):
+        batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    batch.step(150)
+    for d, s in enumerate(specs):
+        single = lbf.Lattice(plist[d], nxs[d], nys[d])
+        single.init_drop(s["R"], s["cx"], s["cy"])
+        single.step(150)
+        fb, gb = batch.populations(d)
+        fs, gs = single.populations()
+        assert np.array_equal(fb, fs) and np.array_equal(gb, gs)
+        single.close()
+
+
+def test_checkpoint_resume_is_bitwise(lbf):
+    p = lbf.params(collision="mrt", precision="fp32", tau_alpha=1.5, tau_beta=0.6,
+                   h_bottom=lbf.lb_wetting_h(60.0))
+    a = lbf.Lattice(p, 90, 45)
+    a.init_drop(18.0, 45.0, -0.5)
+    a.step(77)
+    blob = a.save_state()
+    a.step(123)
+    b = lbf.Lattice(p, 90, 45)
+    b.load_state(blob)
+    assert b.step_count == 77
+    b.step(123)
+    assert a.save_state() == b.save_state()
+
+
+def test_autotune_does_not_change_state_or_results(lbf):
+    p = lbf.params(collision="mrt", precision="fp32", tau_alpha=1.5, tau_beta=0.6)
+    a = lbf.Lattice(p, 300, 200)
+    a.init_random(0.1, 3)
+    a.step(10)
+    before = a.save_state()
+    bx, rows, ms = a.autotune(reps=2)
+    assert bx in (64, 128, 256, 512) and rows >= 1 and ms > 0
+    assert a.save_state() == before
+    a.step(20)
+    b = lbf.Lattice(p, 300, 200)
+    b.init_random(0.1, 3)
+    b.step(30)
+    assert a.save_state()[32:] == b.save_state()[32:]
+
+
+def test_invalid_arguments(lbf):
+    with pytest.raises(lbf.LBError) as e:
+        lbf.Lattice(lbf.params(tau_alpha=0.5, tau_beta=0.5), 16, 16)
+    assert e.value.code == lbf.LB_ERR_INVALID_ARG
+    with pytest.raises(lbf.LBError):
+        lbf.Lattice(lbf.params(), 2, 16)
+    sim = lbf.Lattice(lbf.params(), 16, 16)
+    with pytest.raises(lbf.LBError):
+        sim.set_tile(48, 4)
+    with pytest.raises(lbf.LBError):
+        sim.init_drop(5.0, 8.0, -0.5, dom=1)
+    with pytest.raises(lbf.LBError):
+        sim.step(-1)
+
+
+# ----------------------------------------------- full-size sampled
+def test_full_size_8192_sampled_windows(lbf, orc):
+    """One step of the 8192^2 FP32 MRT workload in the benchmark's launch
+    shape: sampled windows (corners, walls, interior) recomputed by the
+    oracle from the GPU's own input state, plus global conservation."""
+    import torch
+
+    c = lbinputs.SPINODAL_8192
+    n = c["nx"]
+    gp = lbf.params(precision="fp32", **c["params"])
+    sim = lbf.Lattice(gp, n, n)
+    sim.init_random(c["amp"], c["seed"])
+    sim.step(3)
+    st0 = sim.stats()
+    # bands of rows around the windows, read before the step
+    windows = [(0, 64, 0, 3), (n - 64, n, n - 3, n), (4000, 4100, 4000, 4004), (n - 40, n, 0, 2),
+               (0, 40, n - 2, n)]
+    bands = []
+    for (x0, x1, y0, y1) in windows:
+        b0, b1 = max(0, y0 - 2), min(n, y1 + 2)
+        bands.append((b0, *sim.populations_rows(b0, b1 - b0)))  # FP32 widened to FP64
+    sim.step(1)
+    st1 = sim.stats()
+    op = orc.params(**c["params"])
+    for (x0, x1, y0, y1), (b0, fb, gb) in zip(windows, bands):
+        fo, go = orc.step_window(op, n, n, b0, fb, gb, x0, x1, y0, y1)
+        f1, g1 = sim.populations_rows(y0, y1 - y0)
+        assert max_diff(f1[:, :, x0:x1], fo) <= 2e-6
+        assert max_diff(g1[:, :, x0:x1], go) <= 2e-6
+    assert abs(st1["mass"] - st0["mass"]) <= 1e-9 * st0["mass"]
+    assert abs(st1["order"] - st0["order"]) <= 1e-9 * st0["mass"]
+    torch.cuda.synchronize()
