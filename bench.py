@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the fused binary-fluid LB step on GB300.
+
+Headline workload: the 8192 x 8192 spinodal lattice (D2Q9 two-population
+MRT, walls at y = 0 and y = 8191, phi uniform in [-0.1, 0.1) from SplitMix64
+seed 12345, a = kappa = 0.04, Gamma = 0.1, tau_alpha 1.5, tau_beta 0.6), FP32
+deviation storage.  One bench step = one full time step of every node
+(pull-stream, moments, phi stencils with wetting ghosts, Step 2, equilibria,
+MRT collision, store).  The state (9.7 GB) is far larger than L2, so no flush
+is needed between steps.
+
+Printed: one JSON line with MLUPS (whole job), the roofline of the step
+kernel (algorithmic 144 B per node update over its event-timed duration,
+against the measured HBM copy bandwidth), the end-to-end number through the
+C ABI with host buffers, the FP64 oracle on the host cores, and extras: the
+FP64 build (ALU-bound on GB300) and the batched 256-domain workload against
+a per-domain launch loop.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica (weak scaling, no collective
+on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbinputs  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
+BYTES_PER_NODE = {"fp32": 144, "fp64": 288}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0812_1282_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def profile_traffic(name: str):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/<name>.txt,
+    lines 'source_hash: ...' and 'dram_bytes_per_launch: ...'); None when the
+    kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", name + ".txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path:
+                try:
+                    os.unlink(self.path)
+                except OSError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, value: float) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ our arm
+def time_steps(sim, steps, torch):
+    stream = sim.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", tune=True):
+    c = lbinputs.SPINODAL_8192
+    n = c["nx"] * c["ny"]
+    p = lbf.params(precision=precision, **c["params"])
+    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim.init_random(c["amp"], c["seed"])
+    tile = sim.autotune(reps=3) if tune else sim.tile()
+    sim.init_random(c["amp"], c["seed"])
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    launches0 = sim.launch_count
+    barrier(ws)
+    dt = time_steps(sim, steps, torch)
+    barrier(ws)
+    launches = sim.launch_count - launches0
+    st = sim.stats()
+    return sim, dict(seconds=dt, nodes=n, tile=list(tile[:2]), launches=launches,
+                     mass=st["mass"], max_u=st["max_u"], nonfinite=st["nonfinite"])
+
+
+def run_e2e(lbf, torch, steps):
+    """The same job through the public API with host buffers: upload phi0
+    from pinned host memory, run `steps` steps reading the diagnostics back
+    every 100 steps, and download the final phi field."""
+    import numpy as np
+
+    c = lbinputs.SPINODAL_8192
+    nx, ny = c["nx"], c["ny"]
+    phi0 = torch.from_numpy(lbinputs.random_field(nx, ny, c["amp"], c["seed"])).pin_memory()
+    out_phi = torch.empty((ny, nx), dtype=torch.float64).pin_memory()
+    p = lbf.params(precision="fp32", **c["params"])
+    sim = lbf.Lattice(p, nx, ny)
+    sim.autotune(reps=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbf.lib().lb_init_phi(sim.h, 0, ctypes.c_void_p(phi0.data_ptr()), 0)
+    done, d2h = 0, 0
+    stats = lbf.Stats()
+    while done < steps:
+        k = min(100, steps - done)
+        sim.step(k)
+        done += k
+        lbf.lib().lb_moments(sim.h, 0, 0, None, None, None, None, ctypes.byref(stats))
+        d2h += 48
+    lbf.lib().lb_moments(sim.h, 0, 0, None, ctypes.c_void_p(out_phi.data_ptr()), None, None,
+                         None)
+    dt = time.perf_counter() - t0
+    d2h += out_phi.numel() * 8
+    h2d = phi0.numel() * 8
+    ok = bool(np.isfinite(out_phi.numpy()).all())
+    sim.close()
+    return dict(seconds=dt, h2d=h2d, d2h=d2h, finite=ok)
+
+
+def run_fp64(lbf, torch, steps):
+    c = lbinputs.SPINODAL_8192
+    n = c["nx"] * c["ny"]
+    p = lbf.params(precision="fp64", **c["params"])
+    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim.init_random(c["amp"], c["seed"])
+    tile = sim.autotune(reps=1)
+    sim.step(2)
+    dt = time_steps(sim, steps, torch)
+    sim.close()
+    return dict(mlups=n * steps / dt / 1e6, seconds_per_step=dt / steps, tile=list(tile[:2]),
+                gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9)
+
+
+def run_batched(lbf, torch, steps):
+    """256 sessile drops (sides 64..512) in one launch per step, against the
+    same domains stepped one after another (one launch per domain per step)."""
+    specs = lbinputs.batch_specs()
+    plist, nxs, nys = [], [], []
+    for s in specs:
+        plist.append(lbf.params(collision="mrt", precision="fp32", tau_alpha=s["tau_alpha"],
+                                tau_beta=s["tau_beta"], h_bottom=lbf.lb_wetting_h(s["theta"])))
+        nxs.append(s["nx"])
+        nys.append(s["ny"])
+    nodes = sum(a * b for a, b in zip(nxs, nys))
+    batch = lbf.Batch(plist, nxs, nys)
+    for d, s in enumerate(specs):
+        batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    tile = batch.autotune(reps=2)
+    batch.step(4)
+    dt_b = time_steps(batch, steps, torch)
+    batch.close()
+    sims = []
+    for d, s in enumerate(specs):
+        sim = lbf.Lattice(plist[d], nxs[d], nys[d])
+        sim.init_drop(s["R"], s["cx"], s["cy"])
+        sim.set_tile(*tile[:2])
+        sim.step(2)
+        sims.append(sim)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        for sim in sims:
+            sim.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    dt_l = e0.elapsed_time(e1) / 1e3
+    # stronger loop: each domain runs all its steps back to back from its own
+    # captured CUDA graphs, one domain after another
+    e0.record()
+    for sim in sims:
+        sim.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    dt_g = e0.elapsed_time(e1) / 1e3
+    for sim in sims:
+        sim.close()
+    full = 10000
+    return dict(domains=len(specs), nodes=nodes, steps_timed=steps,
+                batched_mlups=nodes * steps / dt_b / 1e6, loop_mlups=nodes * steps / dt_l / 1e6,
+                loop_graph_mlups=nodes * steps / dt_g / 1e6,
+                batched_sims_per_s=len(specs) / (dt_b / steps * full),
+                loop_sims_per_s=len(specs) / (dt_l / steps * full),
+                loop_graph_sims_per_s=len(specs) / (dt_g / steps * full),
+                speedup_vs_loop=dt_l / dt_b, speedup_vs_loop_graph=dt_g / dt_b,
+                tile=list(tile[:2]),
+                note="sims/s of the 10000-step job, from %d timed steps; loop = one launch "
+                     "per domain per step; loop_graph = each domain's steps replayed from "
+                     "its own CUDA graphs, domains in sequence" % steps)
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle, as written, on the host cores: the 512 x 512 cut of
+    the same spinodal workload, stepped until about `seconds` elapse."""
+    import oracle
+
+    c = lbinputs.SPINODAL_8192
+    n = c["sub"]
+    p = oracle.params(**c["params"])
+    lat = oracle.OracleLattice(p, n, n)
+    lat.init_random(c["amp"], c["seed"])
+    lat.step(1)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        lat.step(5)
+        done += 5
+    dt = time.perf_counter() - t0
+    return {"value": n * n * done / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": "%dx%d cut of the 8192^2 spinodal MRT workload, %d FP64 steps (%.1f s)"
+                      % (n, n, done, dt)}
+
+
+def ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    barrier(ws)
+    import paper_0812_1282_gb300 as lbf
+
+    lbf.lib()
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup)
+    clocks = clk.summary()
+    sim.close()
+    torch.cuda.empty_cache()
+    dt = max_over_ranks(ws, head["seconds"])
+    total_updates = head["nodes"] * args.steps * ws
+    value = total_updates / dt / 1e6
+    per_launch = dt / args.steps
+    achieved = head["nodes"] * BYTES_PER_NODE["fp32"] / per_launch / 1e9
+    traffic = profile_traffic("lb_step_mrt_fp32_8192")
+    line = {
+        "metric": "MLUPS (MRT, FP32, 8192^2) and HBM-roofline fraction",
+        "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "spinodal 8192x8192 D2Q9 two-population MRT (FP32 deviation "
+                               "storage), walls y=0/8191, seed 12345",
+                   "nx": 8192, "ny": 8192, "collision": "mrt", "tile": head["tile"],
+                   "l2": "state 9.7 GB >> 129 MB L2, no flush needed",
+                   "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": traffic,
+                     "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind,
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"]},
+        "gpu_launches": head["launches"],
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.quick:
+        e2e = run_e2e(lbf, torch, args.steps)
+        line["e2e"] = {"value": round(head["nodes"] * args.steps / e2e["seconds"] / 1e6, 1),
+                       "unit": "MLUPS", "h2d_bytes_per_step": e2e["h2d"] // args.steps,
+                       "d2h_bytes_per_step": e2e["d2h"] // args.steps,
+                       "job": "phi0 H2D from pinned memory, %d steps, stats D2H every 100 "
+                              "steps, final phi D2H" % args.steps}
+        torch.cuda.empty_cache()
+        extras = {}
+        try:
+            fp64 = run_fp64(lbf, torch, max(4, args.steps // 20))
+            fp64["bound"] = "alu"
+            fp64["alu_peak_tflops_nominal"] = FP64_NOMINAL_TFLOPS
+            extras["fp64"] = fp64
+        except Exception as exc:  # report, do not hide
+            extras["fp64"] = {"error": str(exc)}
+        torch.cuda.empty_cache()
+        try:
+            extras["batched"] = run_batched(lbf, torch, max(20, args.steps // 2))
+        except Exception as exc:
+            extras["batched"] = {"error": str(exc)}
+        line["extras"] = extras
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- reference arm
+def reference(args):
+    """The FP64 oracle on the host cores, on the same workload and metric;
+    each step is one oracle step of the 512x512 cut."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    c = lbinputs.SPINODAL_8192
+    n = c["sub"]
+    lat = oracle.OracleLattice(oracle.params(**c["params"]), n, n)
+    lat.init_random(c["amp"], c["seed"])
+    lat.step(args.warmup)
+    t0 = time.perf_counter()
+    lat.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = n * n * args.steps / dt / 1e6
+    sample = "%dx%d cut of the 8192^2 spinodal MRT workload, %d FP64 steps" % (n, n, args.steps)
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS (MRT, FP32, 8192^2) and HBM-roofline fraction",
+        "value": round(value, 3), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "spinodal 8192x8192 D2Q9 two-population MRT, walls y=0/8191, "
+                               "seed 12345 (oracle runs the 512x512 cut)", "nx": 8192, "ny": 8192},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": oracle.get_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--quick", action="store_true", help="headline line only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

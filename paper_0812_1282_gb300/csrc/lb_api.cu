@@ -13,6 +13,7 @@
 
 #include "../../include/lbfe.h"
 #include "lb_internal.h"
+#include "lb_node.cuh"
 
 using lbfe::DomDesc;
 using lbfe::StatsOut;
@@ -692,7 +693,10 @@ int lb_get_populations_rows(lb_handle* h, int dom, int y0, int nrows, double* f,
             LB_CUDA(cudaStreamSynchronize(h->stream));
             const double rest = which == 0 ? kRest[i] : 0.0;
             double* o = out + i * nn;
-            if (es == 4) {
+            if (es == 4 && which == 1 && i == 0) {
+                const float* t = reinterpret_cast<const float*>(tmp.data());
+                for (size_t k = 0; k < nn; ++k) o[k] = lbfe::G0<float>::decode(t[k]);
+            } else if (es == 4) {
                 const float* t = reinterpret_cast<const float*>(tmp.data());
                 for (size_t k = 0; k < nn; ++k) o[k] = rest + double(t[k]);
             } else {
@@ -726,7 +730,9 @@ int lb_set_populations(lb_handle* h, int dom, const double* f, const double* g)
             for (size_t k = 0; k < nn; ++k) {
                 const size_t q = i * nn + k;
                 const double v = in[q] - rest;
-                if (es == 4)
+                if (es == 4 && which == 1 && i == 0)
+                    reinterpret_cast<float*>(tmp.data())[q] = lbfe::G0<float>::encode(v);
+                else if (es == 4)
                     reinterpret_cast<float*>(tmp.data())[q] = float(v);
                 else
                     reinterpret_cast<double*>(tmp.data())[q] = v;

@@ -15,7 +15,7 @@ template <typename Real, bool MRT>
 __global__ void __launch_bounds__(512) step_single_kernel(DomDesc D, int parity, int rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* ring = reinterpret_cast<Real*>(smem_raw);
+    PhiRep<Real>* ring = reinterpret_cast<PhiRep<Real>*>(smem_raw);
     const int x0 = blockIdx.x * blockDim.x;
     const int y0 = blockIdx.y * rows;
     process_tile<Real, MRT>(D, parity, x0, y0, rows, ring);
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(512) step_batch_kernel(const DomDesc* __restri
                                                          int n_items, int parity)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* ring = reinterpret_cast<Real*>(smem_raw);
+    PhiRep<Real>* ring = reinterpret_cast<PhiRep<Real>*>(smem_raw);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const DomDesc D = descs[w.dom];
@@ -42,7 +42,7 @@ static cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const
                                  int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
                                  cudaStream_t s)
 {
-    const size_t smem = 4 * size_t(bx + 2) * sizeof(Real);
+    const size_t smem = 4 * size_t(bx + 2) * sizeof(PhiRep<Real>);
     if (n_dom == 1 && d_items == nullptr) {
         dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
         step_single_kernel<Real, MRT><<<grid, bx, smem, s>>>(d, parity, rows);
@@ -188,10 +188,9 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
         fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
         ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
         const long long o = (long long)y * pitch + x;
-        for (int i = 0; i < 9; ++i) {
-            fd[i * P + o] = Real(fe[i]);
-            gd[i * P + o] = Real(ge[i]);
-        }
+        for (int i = 0; i < 9; ++i) fd[i * P + o] = Real(fe[i]);
+        gd[o] = G0<Real>::encode(ge[0]);
+        for (int i = 1; i < 9; ++i) gd[i * P + o] = Real(ge[i]);
     }
 }
 
@@ -247,10 +246,9 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
         const int yr = int(k / nx), x = int(k - (long long)yr * nx);
         const long long o = (long long)(row0 + yr) * pitch + x;
         double f[9], g[9];
-        for (int i = 0; i < 9; ++i) {
-            f[i] = double(fs[i * P + o]);
-            g[i] = double(gs[i * P + o]);
-        }
+        for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
+        g[0] = G0<Real>::decode(gs[o]);
+        for (int i = 1; i < 9; ++i) g[i] = double(gs[i * P + o]);
         const double drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
         const double jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
         const double jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
@@ -351,7 +349,8 @@ template <typename Real>
 __device__ __forceinline__ double phi_at_node(const Real* g, long long P, long long o)
 {
     double v[9];
-    for (int i = 0; i < 9; ++i) v[i] = double(g[i * P + o]);
+    v[0] = G0<Real>::decode(g[o]);
+    for (int i = 1; i < 9; ++i) v[i] = double(g[i * P + o]);
     return phi_sum<double>(v);
 }
 

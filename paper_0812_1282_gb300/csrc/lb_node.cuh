@@ -3,11 +3,17 @@
 //
 // Storage is in deviation form for f: the stored value is f_i - t_i with
 // t = (4/9, 1/9 x4, 1/36 x4) the rest-state weights (rho = 1, u = 0), so
-// that rho - 1 and rho*u come out of sums of small numbers.  g is stored
-// as is (its rest state is g_0 = phi, g_i = 0).
+// that rho - 1 and rho*u come out of sums of small numbers.  g_1..g_8 are
+// stored as is (their rest state is 0).  g_0 carries phi itself (|phi| ~ 1),
+// so in FP32 it is stored as a 32-bit fixed-point number with resolution
+// 2^-29 (range +-4) and advanced by an exact integer add of its small
+// conserved increment; FP64 stores it as a double.  See G0<Real>.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
 
 namespace lbfe {
 
@@ -23,24 +29,125 @@ __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 template <>
 __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 
-// phi = sum_i g_i (Eq. moments), always in this order so that every thread
-// that evaluates phi at a node gets the same bits.
+// Storage of g_0.  value(): the number a stored word represents;
+// advance(raw, d): the stored word of value(raw) + d.
+template <typename Real>
+struct G0;
+template <>
+struct G0<float> {
+    static constexpr double kScale = 536870912.0;  // 2^29
+    __device__ __forceinline__ static float value(float raw)
+    {
+        return __int2float_rn(__float_as_int(raw)) * 0x1p-29f;
+    }
+    __device__ __forceinline__ static float advance(float raw, float d)
+    {
+        return __int_as_float(__float_as_int(raw) + __float2int_rn(d * 0x1p29f));
+    }
+    __host__ __device__ static float encode(double v)
+    {
+#ifdef __CUDA_ARCH__
+        return __int_as_float(__double2int_rn(v * kScale));
+#else
+        const int i = int(std::nearbyint(v * kScale));
+        float f;
+        memcpy(&f, &i, sizeof(f));
+        return f;
+#endif
+    }
+    __host__ __device__ static double decode(float raw)
+    {
+#ifdef __CUDA_ARCH__
+        return double(__float_as_int(raw)) / kScale;
+#else
+        int i;
+        memcpy(&i, &raw, sizeof(i));
+        return double(i) / kScale;
+#endif
+    }
+};
+template <>
+struct G0<double> {
+    __device__ __forceinline__ static double value(double raw) { return raw; }
+    __device__ __forceinline__ static double advance(double raw, double d) { return raw + d; }
+    __host__ __device__ static double encode(double v) { return v; }
+    __host__ __device__ static double decode(double raw) { return raw; }
+};
+
+// phi = sum_i g_i (Eq. moments) from stored words, always in this order so
+// that every thread that evaluates phi at a node gets the same bits.
 template <typename Real>
 __device__ __forceinline__ Real phi_sum(const Real (&g)[9])
 {
-    return (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
+    return (((G0<Real>::value(g[0]) + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) +
+           g[8];
 }
 
-// Eq. (best): isotropic gradient (1/12 [-1 0 1; -4 0 4; -1 0 1] and its
-// transpose) and nine-point Laplacian (1/6 [1 4 1; 4 -20 4; 1 4 1]).
+// sum of g_1..g_8
 template <typename Real>
-__device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s, Real ne, Real nw,
-                                         Real se, Real sw, Real& dx, Real& dy, Real& lap)
+__device__ __forceinline__ Real g_tail_sum(const Real (&g)[9])
+{
+    return (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+}
+
+// phi at one node as published for the stencils.  The stencil weights of
+// Eq. (best) sum to zero, so only differences to the centre node matter;
+// in FP32 phi is kept as (fixed-point g_0 word, float sum of g_1..g_8) so
+// that the difference of two nodes is an exact integer difference plus a
+// difference of small numbers, free of the cancellation that rounding phi
+// itself (|phi| ~ 1) would cause.
+template <typename Real>
+struct PhiRep;
+template <>
+struct PhiRep<float> {
+    int q;    // stored g_0 word (value q * 2^-29)
+    float t;  // g_1 + ... + g_8
+    __device__ __forceinline__ static PhiRep make(const float (&g)[9])
+    {
+        return PhiRep{__float_as_int(g[0]), g_tail_sum<float>(g)};
+    }
+    __device__ __forceinline__ float value() const { return __int2float_rn(q) * 0x1p-29f + t; }
+    // the node's phi minus 2h (wetting ghost), h rounded to 2^-30
+    __device__ __forceinline__ PhiRep minus(float two_h) const
+    {
+        return PhiRep{q - __float2int_rn(two_h * 0x1p29f), t};
+    }
+    __device__ __forceinline__ float operator-(const PhiRep& b) const
+    {
+        return __int2float_rn(q - b.q) * 0x1p-29f + (t - b.t);
+    }
+};
+template <>
+struct PhiRep<double> {
+    double v;
+    __device__ __forceinline__ static PhiRep make(const double (&g)[9])
+    {
+        return PhiRep{g[0] + g_tail_sum<double>(g)};
+    }
+    __device__ __forceinline__ double value() const { return v; }
+    __device__ __forceinline__ PhiRep minus(double two_h) const { return PhiRep{v - two_h}; }
+    __device__ __forceinline__ double operator-(const PhiRep& b) const { return v - b.v; }
+};
+
+// Eq. (best): isotropic gradient (1/12 [-1 0 1; -4 0 4; -1 0 1] and its
+// transpose) and nine-point Laplacian (1/6 [1 4 1; 4 -20 4; 1 4 1]),
+// written on the differences d* = phi(neighbour) - phi(centre).
+template <typename Real>
+__device__ __forceinline__ void stencils_diff(Real e, Real w, Real n, Real s, Real ne, Real nw,
+                                              Real se, Real sw, Real& dx, Real& dy, Real& lap)
 {
     const Real c12 = Real(1) / Real(12), c6 = Real(1) / Real(6);
     dx = (Real(4) * (e - w) + (ne - nw) + (se - sw)) * c12;
     dy = (Real(4) * (n - s) + (ne - se) + (nw - sw)) * c12;
-    lap = (Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - Real(20) * c) * c6;
+    lap = (Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw))) * c6;
+}
+
+// Same stencils on absolute values (used where phi is a plain double field).
+template <typename Real>
+__device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s, Real ne, Real nw,
+                                         Real se, Real sw, Real& dx, Real& dy, Real& lap)
+{
+    stencils_diff<Real>(e - c, w - c, n - c, s - c, ne - c, nw - c, se - c, sw - c, dx, dy, lap);
 }
 
 // Equilibria of Appendix A (Eq. equilibrium) for i = 1..8, f in deviation
@@ -96,11 +203,13 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
     ge[8] = ga - c12 * (puy - pux);
 }
 
-// One node of Steps 1-3 (Sec. V): moments of the pulled populations f, g,
+// One node of Steps 1-3 (Sec. V): moments of the pulled populations f, g
+// (g[0] a stored word, see G0),
 // thermodynamics from the phi stencil values, Step 2, equilibria and BGK
 // or MRT collision.  fo, go receive the post-collision populations (f in
-// deviation form).  f'_0 and g'_0 follow from conservation of rho and phi,
-// which both collisions satisfy exactly (Eq. feq0, S_0 = 0).
+// deviation form, go[0] a stored word).  f'_0 and g'_0 follow from
+// conservation of rho and phi, which both collisions satisfy exactly
+// (Eq. feq0, S_0 = 0): g'_0 = g_0 + (sum_{i>0} g_i - sum_{i>0} g'_i).
 //
 // MRT: f' = f - M^-1 S M (f - f^eq) with S = diag(0,1,1,0,1,0,1,w,w) is
 // evaluated as f' = f^eq + M^-1 (I - S) M (f - f^eq): only the momentum
@@ -157,7 +266,7 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
     const Real kg = Real(1) - P.omega_phi;
 #pragma unroll
     for (int i = 1; i < 9; ++i) go[i] = ge[i] + kg * (g[i] - ge[i]);
-    go[0] = phi - ((((go[1] + go[2]) + (go[3] + go[4])) + ((go[5] + go[6]) + (go[7] + go[8]))));
+    go[0] = G0<Real>::advance(g[0], g_tail_sum<Real>(g) - g_tail_sum<Real>(go));
 }
 
 }  // namespace lbfe

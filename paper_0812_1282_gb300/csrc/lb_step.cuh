@@ -70,18 +70,19 @@ __device__ __forceinline__ void pull9(const Real* __restrict__ src, int P, const
 }
 
 template <typename Real>
-__device__ __forceinline__ Real pull_phi(const Real* __restrict__ g, int P, const RowGeo& r, int x,
-                                         int xm, int xp)
+__device__ __forceinline__ PhiRep<Real> pull_phi(const Real* __restrict__ g, int P, const RowGeo& r,
+                                                 int x, int xm, int xp)
 {
     Real v[9];
     pull9<Real>(g, P, r, x, xm, xp, v);
-    return phi_sum<Real>(v);
+    return PhiRep<Real>::make(v);
 }
 
 template <typename Real, bool MRT>
 __device__ __forceinline__ void process_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             Real* __restrict__ ring)
+                                             PhiRep<Real>* __restrict__ ring)
 {
+    using Rep = PhiRep<Real>;
     const Real* __restrict__ fs = static_cast<const Real*>((parity ? D.f[1] : D.f[0]));
     const Real* __restrict__ gs = static_cast<const Real*>((parity ? D.g[1] : D.g[0]));
     Real* __restrict__ fd = static_cast<Real*>((parity ? D.f[0] : D.f[1]));
@@ -109,25 +110,25 @@ __device__ __forceinline__ void process_tile(const DomDesc& D, int parity, int x
     const int y1 = min(y0 + rows, ny);
     const int own = tx + 1, hr = ncols + 1;
 
-    auto slot = [&](int y) -> Real* { return ring + ((y - y0 + 1) & 3) * W; };
+    auto slot = [&](int y) -> Rep* { return ring + ((y - y0 + 1) & 3) * W; };
 
     // pull g of lattice row y, keep it in gv and publish phi there into the
     // ring slot of row ys (ys = y except across the periodic seam)
     auto publish_row = [&](int y, int ys, Real (&gv)[9]) {
         const RowGeo r = row_geo(y, ny, pitch, walls);
         pull9<Real>(gs, P, r, x, xm, xp, gv);
-        Real* s = slot(ys);
-        s[own] = phi_sum<Real>(gv);
+        Rep* s = slot(ys);
+        s[own] = Rep::make(gv);
         if (left) s[0] = pull_phi<Real>(gs, P, r, xl, xlm, xlp);
         if (right) s[hr] = pull_phi<Real>(gs, P, r, xr, xrm, xrp);
     };
     // ghost row yg from the fluid row ys: phi(yg) = phi(ys) - 2h
     auto ghost_row = [&](int yg, int ys, Real h2) {
-        Real* sg = slot(yg);
-        const Real* ss = slot(ys);
-        sg[own] = ss[own] - h2;
-        if (left) sg[0] = ss[0] - h2;
-        if (right) sg[hr] = ss[hr] - h2;
+        Rep* sg = slot(yg);
+        const Rep* ss = slot(ys);
+        sg[own] = ss[own].minus(h2);
+        if (left) sg[0] = ss[0].minus(h2);
+        if (right) sg[hr] = ss[hr].minus(h2);
     };
 
     Real gc[9], gn[9];
@@ -161,15 +162,17 @@ __device__ __forceinline__ void process_tile(const DomDesc& D, int parity, int x
             const RowGeo r = row_geo(y, ny, pitch, walls);
             Real f[9];
             pull9<Real>(fs, P, r, x, xm, xp, f);
-            const Real* sm = slot(y - 1);
-            const Real* sc = slot(y);
-            const Real* sp = slot(y + 1);
+            const Rep* sm = slot(y - 1);
+            const Rep* sc = slot(y);
+            const Rep* sp = slot(y + 1);
+            const Rep c = sc[own];
             Real dx, dy, lap;
-            stencils<Real>(sc[own], sc[own + 1], sc[own - 1], sp[own], sm[own], sp[own + 1],
-                           sp[own - 1], sm[own + 1], sm[own - 1], dx, dy, lap);
+            stencils_diff<Real>(sc[own + 1] - c, sc[own - 1] - c, sp[own] - c, sm[own] - c,
+                                sp[own + 1] - c, sp[own - 1] - c, sm[own + 1] - c,
+                                sm[own - 1] - c, dx, dy, lap);
             const bool s2 = D.step2 && (r.wlo || r.whi);
             Real fo[9], go[9];
-            collide<Real, MRT>(prm, f, gc, sc[own], dx, dy, lap, s2, fo, go);
+            collide<Real, MRT>(prm, f, gc, c.value(), dx, dy, lap, s2, fo, go);
             const int o = r.c + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
