@@ -29,6 +29,28 @@ __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
 template <>
 __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 
+// x / K for a small integer constant K, unbiased.  In FP32 the product with
+// the rounded reciprocal fl(1/K) carries a systematic relative bias (e.g.
+// +3e-8 for K = 3); one FMA residual step removes it (the result is the
+// correctly rounded quotient up to rare ties).  A coherent bias in the
+// equilibrium weights or stencil constants acts like a persistent force and
+// drives a slow drift of the interface, so every division of the node
+// arithmetic goes through here.
+template <int K, typename Real>
+__device__ __forceinline__ Real div_const(Real x);
+template <int K>
+__device__ __forceinline__ float div_const(float x)
+{
+    constexpr float r = 1.0f / float(K);
+    const float q = x * r;
+    return fmaf(fmaf(-q, float(K), x), r, q);
+}
+template <int K>
+__device__ __forceinline__ double div_const(double x)
+{
+    return x / double(K);
+}
+
 // Storage of g_0.  value(): the number a stored word represents;
 // advance(raw, d): the stored word of value(raw) + d.
 template <typename Real>
@@ -136,10 +158,9 @@ template <typename Real>
 __device__ __forceinline__ void stencils_diff(Real e, Real w, Real n, Real s, Real ne, Real nw,
                                               Real se, Real sw, Real& dx, Real& dy, Real& lap)
 {
-    const Real c12 = Real(1) / Real(12), c6 = Real(1) / Real(6);
-    dx = (Real(4) * (e - w) + (ne - nw) + (se - sw)) * c12;
-    dy = (Real(4) * (n - s) + (ne - se) + (nw - sw)) * c12;
-    lap = (Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw))) * c6;
+    dx = div_const<12>(Real(4) * (e - w) + (ne - nw) + (se - sw));
+    dy = div_const<12>(Real(4) * (n - s) + (ne - se) + (nw - sw));
+    lap = div_const<6>(Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)));
 }
 
 // Same stencils on absolute values (used where phi is a plain double field).
@@ -154,53 +175,55 @@ __device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s,
 // form: fe[i] = f^eq_i - t_i, using w_i p0 = t_i rho + w_i a(-phi^2/2 +
 // 3 phi^4/4) (Eq. p0, c = 1).  (jxe, jye) = rho u_eq and (uxe, uye) = u_eq
 // are the equilibrium momentum / velocity (zero at Step-2 nodes).
-// Returns mu (Eq. chempot) for the caller's diagnostics.
+// Written as 36 fe_i and 12 ge_i, whose coefficients (the weights w_i,
+// w^xx, w^yy, w^xy and the 3/2 of the velocity terms, times 36 or 12) are
+// exact, followed by one unbiased division each.
 template <typename Real>
 __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
                                            Real jxe, Real jye, Real uxe, Real uye, Real dx,
                                            Real dy, Real lap, Real (&fe)[9], Real (&ge)[9])
 {
-    const Real c3 = Real(1) / Real(3), c6 = Real(1) / Real(6), c12 = Real(1) / Real(12),
-               c24 = Real(1) / Real(24);
     const Real phi2 = phi * phi;
-    // isotropic part: w_i [p0 - kappa phi lap] minus the rest weight
-    const Real A = drho * c3 + P.a * phi2 * (Real(0.75) * phi2 - Real(0.5)) - P.kappa * phi * lap;
+    // 3 x isotropic part: 3 [p0 - kappa phi lap] - rho (Eq. p0 minus the rest pressure)
+    const Real A3 = drho + P.a * phi2 * (Real(2.25) * phi2 - Real(1.5)) -
+                    Real(3) * P.kappa * phi * lap;
     // rho u_a u_b
     const Real rxx = jxe * uxe, ryy = jye * uye, rxy = jxe * uye;
     const Real ruu = rxx + ryy;
-    // kappa d_a phi d_b phi with the w^xx, w^yy, w^xy tables
+    // kappa d_a phi d_b phi
     const Real kxx = P.kappa * dx * dx, kyy = P.kappa * dy * dy, kxy = P.kappa * dx * dy;
-    const Real kd = -(kxx + kyy) * c24;
-    const Real bx = c3 * (A + Real(1.5) * rxx - Real(0.5) * ruu) + c3 * kxx - c6 * kyy;
-    const Real by = c3 * (A + Real(1.5) * ryy - Real(0.5) * ruu) - c6 * kxx + c3 * kyy;
-    const Real bd = c12 * (A + ruu + Real(3) * rxy) + kd + Real(0.25) * kxy;  // e = +-(1,1)
-    const Real ba = c12 * (A + ruu - Real(3) * rxy) + kd - Real(0.25) * kxy;  // e = +-(-1,1)
-    fe[1] = bx + c3 * jxe;
-    fe[2] = bx - c3 * jxe;
-    fe[3] = by + c3 * jye;
-    fe[4] = by - c3 * jye;
-    fe[5] = bd + c12 * (jxe + jye);
-    fe[6] = bd - c12 * (jxe + jye);
-    fe[7] = ba + c12 * (jye - jxe);
-    fe[8] = ba - c12 * (jye - jxe);
-    // g: w_i [Gamma mu + phi e.u + 3/2 phi (e.u e.u - u.u/3)]
-    const Real mu = P.a * (phi2 * phi - phi) - P.kappa * lap;
+    const Real ksum = kxx + kyy;
+    // 36 fe_i = even part + odd (momentum) part
+    const Real Bx = Real(4) * A3 + Real(18) * rxx - Real(6) * ruu + Real(12) * kxx - Real(6) * kyy;
+    const Real By = Real(4) * A3 + Real(18) * ryy - Real(6) * ruu - Real(6) * kxx + Real(12) * kyy;
+    const Real Bd = A3 + Real(3) * ruu + Real(9) * rxy - Real(1.5) * ksum + Real(9) * kxy;  // +-(1,1)
+    const Real Ba = A3 + Real(3) * ruu - Real(9) * rxy - Real(1.5) * ksum - Real(9) * kxy;  // +-(-1,1)
+    fe[1] = div_const<36>(Bx + Real(12) * jxe);
+    fe[2] = div_const<36>(Bx - Real(12) * jxe);
+    fe[3] = div_const<36>(By + Real(12) * jye);
+    fe[4] = div_const<36>(By - Real(12) * jye);
+    fe[5] = div_const<36>(Bd + Real(3) * (jxe + jye));
+    fe[6] = div_const<36>(Bd - Real(3) * (jxe + jye));
+    fe[7] = div_const<36>(Ba + Real(3) * (jye - jxe));
+    fe[8] = div_const<36>(Ba - Real(3) * (jye - jxe));
+    // g: w_i [Gamma mu + phi e.u + 3/2 phi (e.u e.u - u.u/3)], times 12
+    const Real mu = P.a * (phi2 * phi - phi) - P.kappa * lap;  // Eq. (chempot)
     const Real G = P.gamma * mu;
     const Real pux = phi * uxe, puy = phi * uye;
     const Real pxx = pux * uxe, pyy = puy * uye, pxy = pux * uye;
     const Real puu = pxx + pyy;
-    const Real gx = c3 * (G + Real(1.5) * pxx - Real(0.5) * puu);
-    const Real gy = c3 * (G + Real(1.5) * pyy - Real(0.5) * puu);
-    const Real gd = c12 * (G + puu + Real(3) * pxy);
-    const Real ga = c12 * (G + puu - Real(3) * pxy);
-    ge[1] = gx + c3 * pux;
-    ge[2] = gx - c3 * pux;
-    ge[3] = gy + c3 * puy;
-    ge[4] = gy - c3 * puy;
-    ge[5] = gd + c12 * (pux + puy);
-    ge[6] = gd - c12 * (pux + puy);
-    ge[7] = ga + c12 * (puy - pux);
-    ge[8] = ga - c12 * (puy - pux);
+    const Real Cx = Real(4) * G + Real(6) * pxx - Real(2) * puu;
+    const Real Cy = Real(4) * G + Real(6) * pyy - Real(2) * puu;
+    const Real Cd = G + puu + Real(3) * pxy;
+    const Real Ca = G + puu - Real(3) * pxy;
+    ge[1] = div_const<12>(Cx + Real(4) * pux);
+    ge[2] = div_const<12>(Cx - Real(4) * pux);
+    ge[3] = div_const<12>(Cy + Real(4) * puy);
+    ge[4] = div_const<12>(Cy - Real(4) * puy);
+    ge[5] = div_const<12>(Cd + (pux + puy));
+    ge[6] = div_const<12>(Cd - (pux + puy));
+    ge[7] = div_const<12>(Ca + (puy - pux));
+    ge[8] = div_const<12>(Ca - (puy - pux));
 }
 
 // One node of Steps 1-3 (Sec. V): moments of the pulled populations f, g
@@ -246,8 +269,7 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         const Real m8 = ((f[5] - fe[5]) + (f[6] - fe[6])) - ((f[7] - fe[7]) + (f[8] - fe[8]));
         const Real s = (Real(1) - omega) * Real(0.25);
         const Real c7 = s * m7, c8 = s * m8;
-        const Real c6 = Real(1) / Real(6);
-        const Real cx = (jx - jxe) * c6, cy = (jy - jye) * c6;
+        const Real cx = div_const<6>(jx - jxe), cy = div_const<6>(jy - jye);
         fo[1] = fe[1] + c7 + cx;
         fo[2] = fe[2] + c7 - cx;
         fo[3] = fe[3] - c7 + cy;
