@@ -180,7 +180,7 @@ int lb_save_state(lb_handle* h, void* host_buf, size_t bytes);
 int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes);
 
 /* Launch shape: threads per CTA along x (block_x, a multiple of 32 in
- * [32, 512]) and rows each CTA marches through (rows >= 1).  Results do not
+ * [32, 256]) and rows each CTA marches through (rows >= 1).  Results do not
  * depend on it.  Invalidates captured graphs. */
 int lb_set_tile(lb_handle* h, int block_x, int rows);
 int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
@@ -193,7 +193,9 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
 /* Steps taken since the last initialisation (host-side count). */
 long long lb_step_count(const lb_handle* h);
 
-/* Synchronise the handle's stream (LB_ERR_CUDA on a device error). */
+/* Synchronise the handle's stream.  LB_ERR_CUDA on a device error;
+ * LB_ERR_TIMEOUT if a bounded device-side wait of an earlier step gave up
+ * (its results are then invalid).  lb_moments reports the same. */
 int lb_sync(lb_handle* h);
 
 /* Number of kernel launches this handle has enqueued so far (graph replays

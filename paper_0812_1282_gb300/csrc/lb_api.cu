@@ -43,7 +43,7 @@ int fail(int code, const char* fmt, ...)
 
 constexpr size_t kAlign = 256;
 constexpr int kMinBlockX = 32;
-constexpr int kMaxBlockX = 512;
+constexpr int kMaxBlockX = 256;
 constexpr int kGraphBig = 64;
 constexpr int kGraphSmall = 2;
 constexpr int kChunk = 1 << 20;  // nodes per staging chunk for host field output
@@ -54,17 +54,19 @@ const double kRest[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Row pitch in elements: nx logical columns, kXOff leading columns (two of
+// them periodic ghosts), two trailing ghosts and slack; 128-byte multiple.
 int pitch_for(int nx, int precision)
 {
     const int per128 = precision == LB_FP32 ? 32 : 16;  // elements per 128 bytes
-    return (nx + per128 - 1) / per128 * per128;
+    return (nx + 8 + per128 - 1) / per128 * per128;
 }
 
 // Layout of a handle's device memory.
 struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
-    size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0;
+    size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0;
     size_t total = 0;
     long long item_cap = 0;
     int pts_cap = 0;
@@ -108,6 +110,8 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
     off = align_up(off + sizeof(double) * 2 * pts_cap, kAlign);
     L.count = off;
     off = align_up(off + sizeof(int), kAlign);
+    L.err = off;
+    off = align_up(off + sizeof(unsigned), kAlign);
     L.staging = off;
     off = align_up(off + sizeof(double) * 4 * L.staging_nodes, kAlign);
     L.total = off;
@@ -171,6 +175,7 @@ struct lb_handle {
     double* d_pts() const { return reinterpret_cast<double*>(base + L.pts); }
     int* d_count() const { return reinterpret_cast<int*>(base + L.count); }
     double* d_staging() const { return reinterpret_cast<double*>(base + L.staging); }
+    unsigned* d_err() const { return reinterpret_cast<unsigned*>(base + L.err); }
     size_t elem() const { return precision == LB_FP32 ? 4 : 8; }
 };
 
@@ -260,6 +265,21 @@ int use_device(const lb_handle* h)
     return LB_OK;
 }
 
+// Synchronise the stream and report a device-side timeout recorded by a
+// bounded wait (the word is cleared once reported).
+int sync_and_check(lb_handle* h)
+{
+    unsigned err = 0;
+    LB_CUDA(cudaMemcpyAsync(&err, h->d_err(), sizeof(err), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    if (err != 0) {
+        cudaMemsetAsync(h->d_err(), 0, sizeof(unsigned), h->stream);
+        cudaStreamSynchronize(h->stream);
+        return fail(LB_ERR_TIMEOUT, "a device wait gave up (error word 0x%x)", err);
+    }
+    return LB_OK;
+}
+
 int check_dom(const lb_handle* h, int dom)
 {
     if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
@@ -334,6 +354,8 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         lb_destroy(h);
         return rc;
     };
+    if ((e = cudaError_t(lbfe::prepare_step_kernels())) != cudaSuccess)
+        return bail(fail(LB_ERR_CUDA, "kernel setup failed: %s", cudaGetErrorString(e)));
     if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
             cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -372,6 +394,7 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.tau_c1 = 0.5 * (p.tau_alpha - p.tau_beta);
         D.h_bot = p.h_bottom;
         D.h_top = p.h_top;
+        D.err = h->d_err();
         h->descs.push_back(D);
     }
     if ((e = cudaMemsetAsync(h->base, 0, L.total, h->stream)) != cudaSuccess ||
@@ -602,7 +625,8 @@ int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi, d
     StatsOut so{};
     if (stats)
         LB_CUDA(cudaMemcpyAsync(&so, h->d_stats(), sizeof(StatsOut), cudaMemcpyDeviceToHost, h->stream));
-    LB_CUDA(cudaStreamSynchronize(h->stream));
+    rc = sync_and_check(h);
+    if (rc != LB_OK) return rc;
     if (stats) {
         stats->mass = so.mass;
         stats->order = so.order;
@@ -687,7 +711,8 @@ int lb_get_populations_rows(lb_handle* h, int dom, int y0, int nrows, double* f,
         const unsigned char* src =
             static_cast<const unsigned char*>(which == 0 ? D.f[h->parity] : D.g[h->parity]);
         for (int i = 0; i < 9; ++i) {
-            const unsigned char* plane = src + (size_t(i) * D.plane + size_t(y0) * D.pitch) * es;
+            const unsigned char* plane =
+                src + (size_t(i) * D.plane + size_t(y0) * D.pitch + lbfe::kXOff) * es;
             LB_CUDA(cudaMemcpy2DAsync(tmp.data(), es * D.nx, plane, es * D.pitch, es * D.nx, nrows,
                                       cudaMemcpyDeviceToHost, h->stream));
             LB_CUDA(cudaStreamSynchronize(h->stream));
@@ -738,11 +763,15 @@ int lb_set_populations(lb_handle* h, int dom, const double* f, const double* g)
                     reinterpret_cast<double*>(tmp.data())[q] = v;
             }
         }
-        void* dst = which == 0 ? D.f[h->parity] : D.g[h->parity];
-        LB_CUDA(cudaMemcpy2DAsync(dst, es * D.pitch, tmp.data(), es * D.nx, es * D.nx, 9 * D.ny,
-                                  cudaMemcpyHostToDevice, h->stream));
+        unsigned char* dst = static_cast<unsigned char*>(which == 0 ? D.f[h->parity] : D.g[h->parity]);
+        LB_CUDA(cudaMemcpy2DAsync(dst + lbfe::kXOff * es, es * D.pitch, tmp.data(), es * D.nx,
+                                  es * D.nx, 9 * D.ny, cudaMemcpyHostToDevice, h->stream));
         LB_CUDA(cudaStreamSynchronize(h->stream));
     }
+    const int e = lbfe::launch_fill_ghosts(h->precision, D, h->parity, h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "ghost fill failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    LB_CUDA(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 
@@ -800,8 +829,9 @@ int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes)
 int lb_set_tile(lb_handle* h, int block_x, int rows)
 {
     if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
-    if (block_x < kMinBlockX || block_x > kMaxBlockX || block_x % 32 != 0 || rows < 1)
-        return fail(LB_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 512], rows >= 1");
+    if (block_x < kMinBlockX || block_x > kMaxBlockX || block_x % 32 != 0 || rows < 1 ||
+        lbfe::step_smem_bytes(h->precision, block_x) == 0)
+        return fail(LB_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 256], rows >= 1");
     LB_CUDA(cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     h->block_x = block_x;
@@ -823,7 +853,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     if (reps < 1) reps = 1;
     int max_ny = 0;
     for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
-    const int bxs[] = {64, 128, 256, 512};
+    const int bxs[] = {64, 128, 256};
     const int rws[] = {4, 8, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     LB_CUDA(cudaEventCreate(&e0));
@@ -860,6 +890,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc == LB_OK) rc = sync_and_check(h);
     const int rc2 = lb_set_tile(h, rc == LB_OK ? bb : old_bx, rc == LB_OK ? br : old_rows);
     if (rc != LB_OK) return rc;
     if (rc2 != LB_OK) return rc2;
@@ -874,8 +905,7 @@ long long lb_step_count(const lb_handle* h) { return h ? h->steps : -1; }
 int lb_sync(lb_handle* h)
 {
     if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
-    LB_CUDA(cudaStreamSynchronize(h->stream));
-    return LB_OK;
+    return sync_and_check(h);
 }
 
 long long lb_launch_count(const lb_handle* h) { return h ? h->launches : -1; }

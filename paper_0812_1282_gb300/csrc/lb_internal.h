@@ -6,9 +6,15 @@
 
 namespace lbfe {
 
+// Row layout: logical column x of a row lives at physical column x + kXOff;
+// physical columns kXOff-2, kXOff-1 hold copies of logical nx-2, nx-1 and
+// physical nx+kXOff, nx+kXOff+1 copies of logical 0, 1 (periodic ghosts,
+// kept current by every kernel that writes populations).  pitch >= nx + 8.
+constexpr int kXOff = 4;
+
 // One domain as the kernels see it.  Populations live in two ping-pong
 // buffers; buffer b holds f at f[b] and g at g[b], each 9 planes of
-// `plane` elements (pitch * ny, x fastest, pitch >= nx).
+// `plane` elements (pitch * ny, x fastest).
 struct DomDesc {
     void* f[2];
     void* g[2];
@@ -21,6 +27,7 @@ struct DomDesc {
     double omega_phi;         // 1 / tau_phi
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)
     double h_bot, h_top;      // wetting gradients
+    unsigned* err;            // device error word (bounded waits that gave up)
 };
 
 // A rectangular piece of one domain processed by one CTA: columns
@@ -54,6 +61,15 @@ int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nr
                    double* partials, int max_partials, StatsOut* out, void* stream);
 int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, int* count,
                      int cap, void* stream);
+int launch_fill_ghosts(int precision, const DomDesc& d, int parity, void* stream);
+
+// Opt the step kernels in to large dynamic shared memory (call once per
+// device before the first launch, outside any stream capture).
+int prepare_step_kernels();
+
+// Dynamic shared memory of the step kernel for a block width (0 if the
+// width is not supported for this precision).
+size_t step_smem_bytes(int precision, int block_x);
 
 int max_partials_needed(int nx, int ny);
 

@@ -11,30 +11,62 @@
 namespace lbfe {
 
 // ------------------------------------------------------------------ step
+// Stage-ring depth: rows of bulk copies in flight per CTA.
+template <typename Real>
+constexpr int kStages = sizeof(Real) == 4 ? 4 : 3;
+
+// Launch shape: blockDim.x = W + 32 (one producer warp, W / 32 compute
+// warps), W the strip width.
 template <typename Real, bool MRT>
-__global__ void __launch_bounds__(512) step_single_kernel(DomDesc D, int parity, int rows)
+__global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity, int rows)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PhiRep<Real>* ring = reinterpret_cast<PhiRep<Real>*>(smem_raw);
-    const int x0 = blockIdx.x * blockDim.x;
-    const int y0 = blockIdx.y * rows;
-    process_tile<Real, MRT>(D, parity, x0, y0, rows, ring);
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStages<Real>;
+    const int NW = int(blockDim.x >> 5) - 1;
+    init_stages<Real>(smem, NW, S);
+    const int warp = int(threadIdx.x >> 5);
+    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
+    unsigned q = 0;
+    if (warp == 0) {
+        produce_tile<Real>(D, parity, x0, y0, rows, smem, NW, S, q);
+        drain_stages<Real>(smem, NW, S, q, D.err);
+    } else {
+        consume_tile<Real, MRT>(D, parity, x0, y0, rows, smem, NW, S, warp - 1, q);
+    }
 }
 
 // Persistent form: a fixed grid walks a precomputed list of tiles of many
-// domains (grid-stride, static order).
+// domains (grid-stride, static order); producer and compute warps walk the
+// same list, so the stage ring carries over from tile to tile.
 template <typename Real, bool MRT>
-__global__ void __launch_bounds__(512) step_batch_kernel(const DomDesc* __restrict__ descs,
+__global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restrict__ descs,
                                                          const WorkItem* __restrict__ items,
                                                          int n_items, int parity)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PhiRep<Real>* ring = reinterpret_cast<PhiRep<Real>*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStages<Real>;
+    const int NW = int(blockDim.x >> 5) - 1;
+    init_stages<Real>(smem, NW, S);
+    const int warp = int(threadIdx.x >> 5);
+    unsigned q = 0;
+    unsigned* err = nullptr;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         const DomDesc D = descs[w.dom];
-        process_tile<Real, MRT>(D, parity, w.x0, w.y0, w.rows, ring);
+        err = D.err;
+        if (warp == 0)
+            produce_tile<Real>(D, parity, w.x0, w.y0, w.rows, smem, NW, S, q);
+        else
+            consume_tile<Real, MRT>(D, parity, w.x0, w.y0, w.rows, smem, NW, S, warp - 1, q);
     }
+    if (warp == 0) drain_stages<Real>(smem, NW, S, q, err);
+}
+
+size_t step_smem_bytes(int precision, int bx)
+{
+    if (bx < 32 || bx > 256 || bx % 32) return 0;
+    return precision == 0 ? StageLayout<float>(bx / 32, kStages<float>).total()
+                          : StageLayout<double>(bx / 32, kStages<double>).total();
 }
 
 template <typename Real, bool MRT>
@@ -42,21 +74,44 @@ static cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const
                                  int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
                                  cudaStream_t s)
 {
-    const size_t smem = 4 * size_t(bx + 2) * sizeof(PhiRep<Real>);
+    const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
+    const int threads = bx + 32;
     if (n_dom == 1 && d_items == nullptr) {
         dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
-        step_single_kernel<Real, MRT><<<grid, bx, smem, s>>>(d, parity, rows);
+        step_single_kernel<Real, MRT><<<grid, threads, smem, s>>>(d, parity, rows);
     } else {
         const int grid = grid_p > 0 ? grid_p : n_items;
-        step_batch_kernel<Real, MRT><<<grid, bx, smem, s>>>(d_descs, d_items, n_items, parity);
+        step_batch_kernel<Real, MRT><<<grid, threads, smem, s>>>(d_descs, d_items, n_items, parity);
     }
     return cudaGetLastError();
+}
+
+template <typename Real, bool MRT>
+static cudaError_t allow_large_smem()
+{
+    const int bytes = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(step_single_kernel<Real, MRT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_batch_kernel<Real, MRT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+int prepare_step_kernels()
+{
+    cudaError_t e = allow_large_smem<float, false>();
+    if (e == cudaSuccess) e = allow_large_smem<float, true>();
+    if (e == cudaSuccess) e = allow_large_smem<double, false>();
+    if (e == cudaSuccess) e = allow_large_smem<double, true>();
+    return static_cast<int>(e);
 }
 
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x, int rows,
                 int grid_persistent, void* stream)
 {
+    if (step_smem_bytes(precision, block_x) == 0) return int(cudaErrorInvalidValue);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (precision == 0) {
@@ -71,6 +126,35 @@ int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_desc
                                                 block_x, rows, grid_persistent, s);
     }
     return static_cast<int>(e);
+}
+
+// Periodic ghost columns of every row of the 18 planes of one buffer, from
+// the logical columns they mirror (used after host writes).
+template <typename Real>
+__global__ void fill_ghosts_kernel(DomDesc D, int parity)
+{
+    Real* f = static_cast<Real*>(parity ? D.f[1] : D.f[0]);
+    Real* g = static_cast<Real*>(parity ? D.g[1] : D.g[0]);
+    const long long rows = 9LL * D.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 2 * rows * 4;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int which = int(k & 3);        // ghost column: -2, -1, nx, nx+1
+        const long long rr = (k >> 2) % rows;  // plane * ny + row
+        Real* base = ((k >> 2) < rows ? f : g) + rr * D.pitch + kXOff;
+        const int dst = which < 2 ? which - 2 : D.nx + (which - 2);
+        const int src = which < 2 ? D.nx + which - 2 : which - 2;
+        base[dst] = base[src];
+    }
+}
+
+int launch_fill_ghosts(int precision, const DomDesc& d, int parity, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 0)
+        fill_ghosts_kernel<float><<<64, 256, 0, s>>>(d, parity);
+    else
+        fill_ghosts_kernel<double><<<64, 256, 0, s>>>(d, parity);
+    return static_cast<int>(cudaGetLastError());
 }
 
 // ------------------------------------------------------------ init phi0
@@ -187,10 +271,22 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
         equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge);
         fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
         ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
-        const long long o = (long long)y * pitch + x;
-        for (int i = 0; i < 9; ++i) fd[i * P + o] = Real(fe[i]);
-        gd[o] = G0<Real>::encode(ge[0]);
-        for (int i = 1; i < 9; ++i) gd[i * P + o] = Real(ge[i]);
+        const long long o = (long long)y * pitch + x + kXOff;
+        const long long og1 = x < 2 ? o + nx : -1, og2 = x >= nx - 2 ? o - nx : -1;
+        for (int i = 0; i < 9; ++i) {
+            const Real fv = Real(fe[i]);
+            const Real gv = i == 0 ? G0<Real>::encode(ge[0]) : Real(ge[i]);
+            fd[i * P + o] = fv;
+            gd[i * P + o] = gv;
+            if (og1 >= 0) {
+                fd[i * P + og1] = fv;
+                gd[i * P + og1] = gv;
+            }
+            if (og2 >= 0) {
+                fd[i * P + og2] = fv;
+                gd[i * P + og2] = gv;
+            }
+        }
     }
 }
 
@@ -244,7 +340,7 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int yr = int(k / nx), x = int(k - (long long)yr * nx);
-        const long long o = (long long)(row0 + yr) * pitch + x;
+        const long long o = (long long)(row0 + yr) * pitch + x + kXOff;
         double f[9], g[9];
         for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
         g[0] = G0<Real>::decode(gs[o]);
@@ -364,9 +460,9 @@ __global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count,
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int y = int(k / nx), x = int(k - (long long)y * nx);
-        const double a = phi_at_node(gs, P, (long long)y * pitch + x);
+        const double a = phi_at_node(gs, P, (long long)y * pitch + x + kXOff);
         const int xp = x + 1 == nx ? 0 : x + 1;
-        const double b = phi_at_node(gs, P, (long long)y * pitch + xp);
+        const double b = phi_at_node(gs, P, (long long)y * pitch + xp + kXOff);
         if ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0)) {
             const int idx = atomicAdd(count, 1);
             if (idx < cap) {
@@ -375,7 +471,7 @@ __global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count,
             }
         }
         if (y + 1 < ny) {
-            const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x);
+            const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x + kXOff);
             if ((a > 0.0 && c < 0.0) || (a < 0.0 && c > 0.0)) {
                 const int idx = atomicAdd(count, 1);
                 if (idx < cap) {

@@ -163,7 +163,7 @@ def test_ragged_sizes_and_tile_independence(lbf, orc, nx, ny, walls):
     ref.init_phi(phi0)
     ref.step(40)
     outs = []
-    for bx, rows in [(32, 1), (64, 3), (128, 7), (512, 128), (96, 2)]:
+    for bx, rows in [(32, 1), (64, 3), (128, 7), (256, 128), (96, 2)]:
         sim = lbf.Lattice(lbf.params(precision="fp64", **kw), nx, ny)
         sim.set_tile(bx, rows)
         sim.init_phi(phi0)
