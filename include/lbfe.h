@@ -205,6 +205,33 @@ long long lb_launch_count(const lb_handle* h);
 const char* lb_error_string(int code);
 const char* lb_last_error(void);
 
+/* Diagnostics without any allocation (the paper has no counterpart: this is
+ * a service for callers that may not allocate device memory at the time
+ * they need the numbers -- code running inside a CUDA graph capture, code
+ * that owns all device memory through its own pool, long-running services
+ * that must keep a fixed footprint).
+ *  f, g:      device arrays [9][ny][nx] of absolute populations (the layout
+ *             lb_get_populations returns), float for LB_FP32, double for
+ *             LB_FP64; owned by the caller.  The call runs on the device
+ *             that holds f.
+ *  stats_dev: device array of 6 doubles, owned by the caller, receiving
+ *             sum rho, sum phi, sum rho u_x, sum rho u_y, max |u| and the
+ *             number of nodes whose moments are not finite.
+ * Work is enqueued on `stream` (cudaStream_t, NULL = legacy default) and
+ * nothing is synchronised.  The scratch space is a fixed device array of
+ * 1024 block partials (48 KiB) that the library carries on every device it
+ * is loaded on until the process exits; its address is looked up on the
+ * first call made on a device, so make that first call outside any stream
+ * capture.  All calls share that array: calls that may overlap on the GPU
+ * (unordered streams) race and can return wrong numbers.  At most
+ * LB_STATS_NOALLOC_MAX_VALUES population values per array (9 * nx * ny);
+ * larger inputs, nx or ny < 1, NULL pointers or an unknown precision give
+ * LB_ERR_INVALID_ARG; a failed launch gives LB_ERR_CUDA.  No cudaMalloc,
+ * cudaFree or other allocating call is made. */
+#define LB_STATS_NOALLOC_MAX_VALUES 2147483647LL
+int lb_stats_noalloc(const void* f, const void* g, int nx, int ny, int precision,
+                     double* stats_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

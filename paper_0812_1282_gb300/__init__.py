@@ -37,6 +37,7 @@ EXPORTS = (
     "lb_wetting_h", "lb_get_populations", "lb_get_populations_rows", "lb_set_populations", "lb_state_bytes",
     "lb_save_state", "lb_load_state", "lb_set_tile", "lb_get_tile", "lb_autotune",
     "lb_step_count", "lb_sync", "lb_launch_count", "lb_error_string", "lb_last_error",
+    "lb_stats_noalloc",
 )
 
 
@@ -127,6 +128,7 @@ def lib():
                 "lb_launch_count": (ll, [_H]),
                 "lb_error_string": (ctypes.c_char_p, [i]),
                 "lb_last_error": (ctypes.c_char_p, []),
+                "lb_stats_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -157,6 +159,19 @@ def lb_device_bytes(precision, nx, ny) -> int:
     ny = np.ascontiguousarray(np.atleast_1d(ny), dtype=np.int32)
     return int(lib().lb_device_bytes(int(precision), len(nx), nx.ctypes.data_as(_I),
                                      ny.ctypes.data_as(_I)))
+
+
+def lb_stats_noalloc(f_dev_ptr, g_dev_ptr, nx, ny, precision, stats_dev_ptr, stream_ptr=0):
+    """Diagnostics of caller-owned device population arrays into a
+    caller-owned device buffer of 6 doubles, without allocating (see
+    include/lbfe.h).  Pointers are integers (e.g. tensor.data_ptr())."""
+    L = lib()
+    rc = L.lb_stats_noalloc(ctypes.c_void_p(f_dev_ptr), ctypes.c_void_p(g_dev_ptr), int(nx),
+                            int(ny), int(precision), ctypes.c_void_p(stats_dev_ptr),
+                            ctypes.c_void_p(stream_ptr))
+    if rc != LB_OK:  # this entry point leaves no message behind (it allocates nothing)
+        raise LBError(rc, "lb_stats_noalloc: %s" % L.lb_error_string(rc).decode())
+    return rc
 
 
 def _torch():
