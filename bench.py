@@ -174,14 +174,19 @@ def time_steps(sim, steps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", tune=True):
+def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", size=None, tile=None):
     c = lbinputs.SPINODAL_8192
-    n = c["nx"] * c["ny"]
+    nx = ny = size or c["nx"]
+    n = nx * ny
     p = lbf.params(precision=precision, **c["params"])
-    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim = lbf.Lattice(p, nx, ny)
     sim.init_random(c["amp"], c["seed"])
-    tile = sim.autotune(reps=3) if tune else sim.tile()
-    sim.init_random(c["amp"], c["seed"])
+    if tile:
+        sim.set_tile(*tile)
+        tile = sim.tile()
+    else:
+        tile = sim.autotune(reps=3)
+        sim.init_random(c["amp"], c["seed"])
     sim.step(warmup)
     torch.cuda.synchronize()
     launches0 = sim.launch_count
@@ -345,26 +350,28 @@ def ours(args):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
 
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
     with ClockSampler(torch.cuda.current_device()) as clk:
-        sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup)
+        sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup, size=args.size, tile=tile)
     clocks = clk.summary()
     sim.close()
     torch.cuda.empty_cache()
+    side = args.size or 8192
     dt = max_over_ranks(ws, head["seconds"])
     total_updates = head["nodes"] * args.steps * ws
     value = total_updates / dt / 1e6
     per_launch = dt / args.steps
     achieved = head["nodes"] * BYTES_PER_NODE["fp32"] / per_launch / 1e9
-    traffic = profile_traffic("lb_step_mrt_fp32_8192")
+    traffic = profile_traffic("lb_step_mrt_fp32_8192") if side == 8192 else None
     line = {
         "metric": "MLUPS (MRT, FP32, 8192^2) and HBM-roofline fraction",
         "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "spinodal 8192x8192 D2Q9 two-population MRT (FP32 deviation "
-                               "storage), walls y=0/8191, seed 12345",
-                   "nx": 8192, "ny": 8192, "collision": "mrt", "tile": head["tile"],
+        "config": {"workload": "spinodal %dx%d D2Q9 two-population MRT (FP32 deviation "
+                               "storage), walls y=0/%d, seed 12345" % (side, side, side - 1),
+                   "nx": side, "ny": side, "collision": "mrt", "tile": head["tile"],
                    "l2": "state 9.7 GB >> 129 MB L2, no flush needed",
                    "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
@@ -448,6 +455,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--quick", action="store_true", help="headline line only")
+    ap.add_argument("--size", type=int, default=None,
+                    help="side of a smaller square lattice (profiling aid; default 8192)")
+    ap.add_argument("--tile", default=None,
+                    help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -395,6 +395,14 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.h_bot = p.h_bottom;
         D.h_top = p.h_top;
         D.err = h->d_err();
+        D.fa = float(D.a);
+        D.fkappa = float(D.kappa);
+        D.fgamma = float(D.gamma);
+        D.fomega_phi = float(D.omega_phi);
+        D.ftau_c0 = float(D.tau_c0);
+        D.ftau_c1 = float(D.tau_c1);
+        D.fh_bot = float(D.h_bot);
+        D.fh_top = float(D.h_top);
         h->descs.push_back(D);
     }
     if ((e = cudaMemsetAsync(h->base, 0, L.total, h->stream)) != cudaSuccess ||

@@ -71,6 +71,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Same test, but a thread that finds the phase incomplete sleeps until it
+// completes or about `ns` nanoseconds pass (no busy polling).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -90,15 +105,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
     if (mbar_try_wait(bar, parity)) return true;
     if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
     const unsigned long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0) {
-            if (global_ns() - t0 > kWaitNs) {
-                if (err) atomicOr(err, kErrTimeout);
-                return false;
-            }
-            if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (global_ns() - t0 > kWaitNs) {
+            if (err) atomicOr(err, kErrTimeout);
+            return false;
         }
+        if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
     }
 }
 

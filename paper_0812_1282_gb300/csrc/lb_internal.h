@@ -28,6 +28,9 @@ struct DomDesc {
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)
     double h_bot, h_top;      // wetting gradients
     unsigned* err;            // device error word (bounded waits that gave up)
+    // the same parameters rounded to float once on the host (the FP32 step
+    // reads these; converting in the kernel would run on the slow FP64 pipe)
+    float fa, fkappa, fgamma, fomega_phi, ftau_c0, ftau_c1, fh_bot, fh_top;
 };
 
 // A rectangular piece of one domain processed by one CTA: columns

@@ -23,15 +23,15 @@ __global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity,
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStages<Real>;
     const int NW = int(blockDim.x >> 5) - 1;
-    init_stages<Real>(smem, NW, S);
+    init_stages<Real, S>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
     const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
     unsigned q = 0;
     if (warp == 0) {
-        produce_tile<Real>(D, parity, x0, y0, rows, smem, NW, S, q);
-        drain_stages<Real>(smem, NW, S, q, D.err);
+        produce_tile<Real, S>(D, parity, x0, y0, rows, smem, NW, q);
+        drain_stages<Real, S>(smem, NW, q, D.err);
     } else {
-        consume_tile<Real, MRT>(D, parity, x0, y0, rows, smem, NW, S, warp - 1, q);
+        consume_tile<Real, MRT, S>(D, parity, x0, y0, rows, smem, NW, warp - 1, q);
     }
 }
 
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStages<Real>;
     const int NW = int(blockDim.x >> 5) - 1;
-    init_stages<Real>(smem, NW, S);
+    init_stages<Real, S>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
     unsigned q = 0;
     unsigned* err = nullptr;
@@ -55,11 +55,11 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
         const DomDesc D = descs[w.dom];
         err = D.err;
         if (warp == 0)
-            produce_tile<Real>(D, parity, w.x0, w.y0, w.rows, smem, NW, S, q);
+            produce_tile<Real, S>(D, parity, w.x0, w.y0, w.rows, smem, NW, q);
         else
-            consume_tile<Real, MRT>(D, parity, w.x0, w.y0, w.rows, smem, NW, S, warp - 1, q);
+            consume_tile<Real, MRT, S>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
     }
-    if (warp == 0) drain_stages<Real>(smem, NW, S, q, err);
+    if (warp == 0) drain_stages<Real, S>(smem, NW, q, err);
 }
 
 size_t step_smem_bytes(int precision, int bx)

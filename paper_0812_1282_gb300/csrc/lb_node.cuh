@@ -7,7 +7,9 @@
 // stored as is (their rest state is 0).  g_0 carries phi itself (|phi| ~ 1),
 // so in FP32 it is stored as a 32-bit fixed-point number with resolution
 // 2^-29 (range +-4) and advanced by an exact integer add of its small
-// conserved increment; FP64 stores it as a double.  See G0<Real>.
+// conserved increment; FP64 stores it as a double.  See G0<Real>.  (On
+// this GPU integer/float conversions issue on the slow FP64 pipe, so a node
+// converts its g_0 word once, when its phi is formed, and once back.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,10 +47,14 @@ __device__ __forceinline__ float div_const(float x)
     const float q = x * r;
     return fmaf(fmaf(-q, float(K), x), r, q);
 }
+// In FP64 the rounded reciprocal's bias (~1e-16) is far below anything the
+// double build is checked at, and an IEEE division costs about fifteen
+// instructions on the slow FP64 pipe, so a plain product is used.
 template <int K>
 __device__ __forceinline__ double div_const(double x)
 {
-    return x / double(K);
+    constexpr double r = 1.0 / double(K);
+    return x * r;
 }
 
 // Storage of g_0.  value(): the number a stored word represents;
@@ -112,48 +118,10 @@ __device__ __forceinline__ Real g_tail_sum(const Real (&g)[9])
     return (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
 }
 
-// phi at one node as published for the stencils.  The stencil weights of
-// Eq. (best) sum to zero, so only differences to the centre node matter;
-// in FP32 phi is kept as (fixed-point g_0 word, float sum of g_1..g_8) so
-// that the difference of two nodes is an exact integer difference plus a
-// difference of small numbers, free of the cancellation that rounding phi
-// itself (|phi| ~ 1) would cause.
-template <typename Real>
-struct PhiRep;
-template <>
-struct PhiRep<float> {
-    int q;    // stored g_0 word (value q * 2^-29)
-    float t;  // g_1 + ... + g_8
-    __device__ __forceinline__ static PhiRep make(const float (&g)[9])
-    {
-        return PhiRep{__float_as_int(g[0]), g_tail_sum<float>(g)};
-    }
-    __device__ __forceinline__ float value() const { return __int2float_rn(q) * 0x1p-29f + t; }
-    // the node's phi minus 2h (wetting ghost), h rounded to 2^-30
-    __device__ __forceinline__ PhiRep minus(float two_h) const
-    {
-        return PhiRep{q - __float2int_rn(two_h * 0x1p29f), t};
-    }
-    __device__ __forceinline__ float operator-(const PhiRep& b) const
-    {
-        return __int2float_rn(q - b.q) * 0x1p-29f + (t - b.t);
-    }
-};
-template <>
-struct PhiRep<double> {
-    double v;
-    __device__ __forceinline__ static PhiRep make(const double (&g)[9])
-    {
-        return PhiRep{g[0] + g_tail_sum<double>(g)};
-    }
-    __device__ __forceinline__ double value() const { return v; }
-    __device__ __forceinline__ PhiRep minus(double two_h) const { return PhiRep{v - two_h}; }
-    __device__ __forceinline__ double operator-(const PhiRep& b) const { return v - b.v; }
-};
-
 // Eq. (best): isotropic gradient (1/12 [-1 0 1; -4 0 4; -1 0 1] and its
 // transpose) and nine-point Laplacian (1/6 [1 4 1; 4 -20 4; 1 4 1]),
-// written on the differences d* = phi(neighbour) - phi(centre).
+// written on the differences d* = phi(neighbour) - phi(centre) (the weights
+// sum to zero; near a bulk phase the differences of nearby values are exact).
 template <typename Real>
 __device__ __forceinline__ void stencils_diff(Real e, Real w, Real n, Real s, Real ne, Real nw,
                                               Real se, Real sw, Real& dx, Real& dy, Real& lap)
@@ -163,7 +131,7 @@ __device__ __forceinline__ void stencils_diff(Real e, Real w, Real n, Real s, Re
     lap = div_const<6>(Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)));
 }
 
-// Same stencils on absolute values (used where phi is a plain double field).
+// Same stencils on absolute values.
 template <typename Real>
 __device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s, Real ne, Real nw,
                                          Real se, Real sw, Real& dx, Real& dy, Real& lap)

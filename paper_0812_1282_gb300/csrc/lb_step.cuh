@@ -9,7 +9,9 @@
 // for direction i the segment of plane i at row r - e_iy (or plane opp(i)
 // at row r for a bounce-back link), columns x0-4 .. x0+W+4.  A stage thus
 // holds exactly the 9 f and 9 g values every node of row r pulls, at column
-// offsets -1/0/+1.  Stages live in an S-slot ring; slot k has a "full"
+// offsets -1/0/+1 (the two rows just outside the tile are only read for
+// their phi, so only their 9 g segments are copied).  Stages live in an
+// S-slot ring; slot k has a "full"
 // mbarrier (completed by the copies' transaction bytes) and an "empty"
 // mbarrier (one arrival per compute warp that is done with it).
 //
@@ -17,7 +19,7 @@
 // and runs independently of the other compute warps:
 //   1. wait until the stage of row y+1 is full, compute phi there for its 32
 //      columns and (lanes 0 / 31) the two halo columns, into a warp-private
-//      4-row ring of PhiRep (wetting ghost rows outside the walls);
+//      4-row ring of phi values (wetting ghost rows outside the walls);
 //   2. read f and g of row y from its stage, take the 3x3 phi stencil from
 //      the ring, collide, store 18 values, and release the stage.
 // Nothing but the stage ring couples the warps, so no CTA-wide barrier sits
@@ -40,18 +42,18 @@
 namespace lbfe {
 
 template <typename Real>
-__device__ __forceinline__ NodeParams<Real> node_params(const DomDesc& D)
+__device__ __forceinline__ NodeParams<Real> node_params(const DomDesc& D);
+template <>
+__device__ __forceinline__ NodeParams<float> node_params<float>(const DomDesc& D)
 {
-    NodeParams<Real> P;
-    P.a = Real(D.a);
-    P.kappa = Real(D.kappa);
-    P.gamma = Real(D.gamma);
-    P.omega_phi = Real(D.omega_phi);
-    P.tau_c0 = Real(D.tau_c0);
-    P.tau_c1 = Real(D.tau_c1);
-    P.h_bot = Real(D.h_bot);
-    P.h_top = Real(D.h_top);
-    return P;
+    return NodeParams<float>{D.fa,      D.fkappa,  D.fgamma, D.fomega_phi,
+                             D.ftau_c0, D.ftau_c1, D.fh_bot, D.fh_top};
+}
+template <>
+__device__ __forceinline__ NodeParams<double> node_params<double>(const DomDesc& D)
+{
+    return NodeParams<double>{D.a,      D.kappa,  D.gamma, D.omega_phi,
+                              D.tau_c0, D.tau_c1, D.h_bot, D.h_top};
 }
 
 // velocity y-components in the paper's order, and the opposite direction
@@ -82,7 +84,7 @@ __device__ __forceinline__ void read9(const Real* __restrict__ s, int segw, int 
 
 // Shared-memory carve-up for one CTA of NW compute warps (byte offsets):
 // S full + S empty mbarriers, S stages of 18 segments of W + 8 elements,
-// and one 4-row phi ring of 34 entries per compute warp.
+// and one 4-row ring of 34 phi values per compute warp.
 template <typename Real>
 struct StageLayout {
     int NW, S, W, segw;
@@ -97,7 +99,7 @@ struct StageLayout {
     }
     __host__ __device__ size_t total() const
     {
-        return rings() + size_t(NW) * 4 * 34 * sizeof(PhiRep<Real>);
+        return rings() + size_t(NW) * 4 * 34 * sizeof(Real);
     }
 };
 
@@ -116,10 +118,9 @@ struct TileRows {
 // ----------------------------------------------------------- producer
 // Warp 0: issue the stages of one tile.  q counts the stages this CTA has
 // issued so far (it continues across tiles of a persistent CTA).
-template <typename Real>
+template <typename Real, int S>
 __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             unsigned char* __restrict__ smem, int NW, int S,
-                                             unsigned& q)
+                                             unsigned char* __restrict__ smem, int NW, unsigned& q)
 {
     const Real* __restrict__ fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
     const Real* __restrict__ gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
@@ -146,12 +147,14 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
         if (use > 0) mbar_wait(empty + slot, (use - 1) & 1u, D.err);
         int r = T.first + p;
         r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        // rows y0-1 and y1 serve only the phi look-ahead: g segments only
+        const bool g_only = (p == 0 && T.first < y0) || (p == T.count() - 1 && T.last >= T.y1);
         if (lane == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(full + slot, 18u * segbytes);
+            mbar_arrive_expect_tx(full + slot, (g_only ? 9u : 18u) * segbytes);
         }
         __syncwarp();
-        if (lane < 18) {
+        if (lane < 18 && !(g_only && lane < 9)) {
             const bool blo = walls && r == 0, bhi = walls && r == ny - 1;
             int pl = i, rr;
             if ((ey > 0 && blo) || (ey < 0 && bhi)) {
@@ -172,12 +175,11 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
 // ----------------------------------------------------------- consumer
 // Compute warp cw (0-based among compute warps) processes its 32 columns of
 // one tile.  q: stage sequence number of the tile's first stage.
-template <typename Real, bool MRT>
+template <typename Real, bool MRT, int S>
 __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             unsigned char* __restrict__ smem, int NW, int S,
-                                             int cw, unsigned& q)
+                                             unsigned char* __restrict__ smem, int NW, int cw,
+                                             unsigned& q)
 {
-    using Rep = PhiRep<Real>;
     Real* __restrict__ fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
     Real* __restrict__ gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
     const int nx = D.nx, ny = D.ny, pitch = D.pitch;
@@ -189,7 +191,7 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
     const Real* stage = reinterpret_cast<const Real*>(smem + L.stages());
-    Rep* ring = reinterpret_cast<Rep*>(smem + L.rings()) + cw * 4 * 34;
+    Real* ring = reinterpret_cast<Real*>(smem + L.rings()) + cw * 4 * 34;
 
     const int lane = threadIdx.x & 31;
     const TileRows T(y0, rows, ny, walls);
@@ -216,31 +218,31 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + slot_of(p));
     };
-    auto rslot = [&](int y) -> Rep* { return ring + ((y - y0 + 1) & 3) * 34; };
+    auto rslot = [&](int y) -> Real* { return ring + ((y - y0 + 1) & 3) * 34; };
     auto wrap_row = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
     // phi of lattice row r (staged at position p) into the ring slot of row ys
     auto publish = [&](int p, int r, int ys) {
         const Real* sg = stage_ptr(p) + 9 * segw;
         const bool blo = walls && r == 0, bhi = walls && r == ny - 1;
-        Rep* s = rslot(ys);
+        Real* s = rslot(ys);
         Real v[9];
         read9<Real>(sg, segw, ci, blo, bhi, v);
-        s[own] = Rep::make(v);
+        s[own] = phi_sum<Real>(v);
         if (left) {
             read9<Real>(sg, segw, cl, blo, bhi, v);
-            s[0] = Rep::make(v);
+            s[0] = phi_sum<Real>(v);
         }
         if (right) {
             read9<Real>(sg, segw, cr, blo, bhi, v);
-            s[hr] = Rep::make(v);
+            s[hr] = phi_sum<Real>(v);
         }
     };
     auto ghost_row = [&](int yg, int ys, Real h2) {
-        Rep* sg = rslot(yg);
-        const Rep* ss = rslot(ys);
-        sg[own] = ss[own].minus(h2);
-        if (left) sg[0] = ss[0].minus(h2);
-        if (right) sg[hr] = ss[hr].minus(h2);
+        Real* sg = rslot(yg);
+        const Real* ss = rslot(ys);
+        sg[own] = ss[own] - h2;
+        if (left) sg[0] = ss[0] - h2;
+        if (right) sg[hr] = ss[hr] - h2;
     };
 
     const int first = T.first, y1 = T.y1;
@@ -282,17 +284,16 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
             Real f[9], g[9];
             read9<Real>(sb, segw, ci, blo, bhi, f);
             read9<Real>(sb + 9 * segw, segw, ci, blo, bhi, g);
-            const Rep* sm = rslot(y - 1);
-            const Rep* sc = rslot(y);
-            const Rep* sp = rslot(y + 1);
-            const Rep c = sc[own];
+            const Real* sm = rslot(y - 1);
+            const Real* sc = rslot(y);
+            const Real* sp = rslot(y + 1);
+            const Real c = sc[own];
             Real dx, dy, lap;
-            stencils_diff<Real>(sc[own + 1] - c, sc[own - 1] - c, sp[own] - c, sm[own] - c,
-                                sp[own + 1] - c, sp[own - 1] - c, sm[own + 1] - c,
-                                sm[own - 1] - c, dx, dy, lap);
+            stencils<Real>(c, sc[own + 1], sc[own - 1], sp[own], sm[own], sp[own + 1],
+                           sp[own - 1], sm[own + 1], sm[own - 1], dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
             Real fo[9], go[9];
-            collide<Real, MRT>(prm, f, g, c.value(), dx, dy, lap, s2, fo, go);
+            collide<Real, MRT>(prm, f, g, c, dx, dy, lap, s2, fo, go);
             const int o = y * pitch + x + kXOff;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -322,8 +323,8 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
     if (T.last >= y1 && !(walls && y1 == ny)) release(T.count() - 1);
 }
 
-template <typename Real>
-__device__ __forceinline__ void init_stages(unsigned char* smem, int NW, int S)
+template <typename Real, int S>
+__device__ __forceinline__ void init_stages(unsigned char* smem, int NW)
 {
     const StageLayout<Real> L(NW, S);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
@@ -341,8 +342,8 @@ __device__ __forceinline__ void init_stages(unsigned char* smem, int NW, int S)
 // Before the producer warp exits, every bulk copy it issued must have
 // landed (they all have unless a wait timed out; this bounded wait covers
 // that case).
-template <typename Real>
-__device__ __forceinline__ void drain_stages(unsigned char* smem, int NW, int S, unsigned q,
+template <typename Real, int S>
+__device__ __forceinline__ void drain_stages(unsigned char* smem, int NW, unsigned q,
                                              unsigned* err)
 {
     if (threadIdx.x != 0 || q == 0) return;
