@@ -205,6 +205,14 @@ long long lb_launch_count(const lb_handle* h);
 const char* lb_error_string(int code);
 const char* lb_last_error(void);
 
+/* Self-check of the device-side wait bound used by the step kernel (the
+ * paper has no counterpart): one warp waits on a barrier that nothing ever
+ * completes; the wait must give up after its wall-time bound (200 ms) and
+ * report it.  Returns LB_ERR_TIMEOUT when the bound works (the expected
+ * result), LB_OK if the wait was satisfied (a defect), LB_ERR_CUDA on a
+ * launch error.  Synchronises `stream`; leaves the context usable. */
+int lb_check_wait_timeout(void* stream);
+
 /* Diagnostics without any allocation (the paper has no counterpart: this is
  * a service for callers that may not allocate device memory at the time
  * they need the numbers -- code running inside a CUDA graph capture, code

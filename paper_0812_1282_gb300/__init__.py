@@ -37,7 +37,7 @@ EXPORTS = (
     "lb_wetting_h", "lb_get_populations", "lb_get_populations_rows", "lb_set_populations", "lb_state_bytes",
     "lb_save_state", "lb_load_state", "lb_set_tile", "lb_get_tile", "lb_autotune",
     "lb_step_count", "lb_sync", "lb_launch_count", "lb_error_string", "lb_last_error",
-    "lb_stats_noalloc",
+    "lb_stats_noalloc", "lb_check_wait_timeout",
 )
 
 
@@ -129,6 +129,7 @@ def lib():
                 "lb_error_string": (ctypes.c_char_p, [i]),
                 "lb_last_error": (ctypes.c_char_p, []),
                 "lb_stats_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
+                "lb_check_wait_timeout": (i, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -172,6 +173,12 @@ def lb_stats_noalloc(f_dev_ptr, g_dev_ptr, nx, ny, precision, stats_dev_ptr, str
     if rc != LB_OK:  # this entry point leaves no message behind (it allocates nothing)
         raise LBError(rc, "lb_stats_noalloc: %s" % L.lb_error_string(rc).decode())
     return rc
+
+
+def lb_check_wait_timeout(stream_ptr=0) -> int:
+    """Run the bounded-wait self-check; returns the status code
+    (LB_ERR_TIMEOUT is the expected, healthy answer)."""
+    return int(lib().lb_check_wait_timeout(ctypes.c_void_p(stream_ptr)))
 
 
 def _torch():

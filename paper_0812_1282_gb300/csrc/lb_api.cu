@@ -918,6 +918,15 @@ int lb_sync(lb_handle* h)
 
 long long lb_launch_count(const lb_handle* h) { return h ? h->launches : -1; }
 
+int lb_check_wait_timeout(void* stream)
+{
+    unsigned word = 0;
+    const int e = lbfe::run_wait_selfcheck(stream, &word);
+    if (e != 0) return fail(LB_ERR_CUDA, "self-check launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    if (word != 0) return fail(LB_ERR_TIMEOUT, "bounded wait gave up as designed (word 0x%x)", word);
+    return LB_OK;
+}
+
 const char* lb_error_string(int code)
 {
     switch (code) {

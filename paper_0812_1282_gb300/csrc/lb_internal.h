@@ -76,4 +76,7 @@ size_t step_smem_bytes(int precision, int block_x);
 
 int max_partials_needed(int nx, int ny);
 
+// Launch the bounded-wait self-check and return the error word it left.
+int run_wait_selfcheck(void* stream, unsigned* word);
+
 }  // namespace lbfe

@@ -497,4 +497,35 @@ int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, i
     return static_cast<int>(cudaGetLastError());
 }
 
+// ------------------------------------------------ bounded-wait self-check
+// One warp waits on an mbarrier that nothing ever completes.  The wait must
+// give up after its wall-time bound and record the failure in the word.
+static __device__ unsigned g_selfcheck_err;
+
+__global__ void wait_selfcheck_kernel()
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    mbar_wait(&bar, 0, &g_selfcheck_err);
+}
+
+int run_wait_selfcheck(void* stream, unsigned* word)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned zero = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_selfcheck_err, &zero, sizeof(zero), 0,
+                                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return int(e);
+    wait_selfcheck_kernel<<<1, 32, 0, s>>>();
+    if ((e = cudaGetLastError()) != cudaSuccess) return int(e);
+    e = cudaMemcpyFromSymbolAsync(word, g_selfcheck_err, sizeof(unsigned), 0,
+                                  cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return int(e);
+    return int(cudaStreamSynchronize(s));
+}
+
 }  // namespace lbfe
