@@ -266,9 +266,9 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
         double dx, dy, lap;
         stencils<double>(v[1][1], v[1][2], v[1][0], v[2][1], v[0][1], v[2][2], v[2][0], v[0][2],
                          v[0][0], dx, dy, lap);
-        double fe[9], ge[9];
+        double fe[9], ge[9], m7eq, m8eq;
         const double phi = v[1][1];
-        equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge);
+        equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge, m7eq, m8eq);
         fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
         ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
         const long long o = (long long)y * pitch + x + kXOff;

@@ -131,12 +131,27 @@ __device__ __forceinline__ void stencils_diff(Real e, Real w, Real n, Real s, Re
     lap = div_const<6>(Real(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)));
 }
 
-// Same stencils on absolute values.
+// Same stencils on absolute values.  FP32 forms the differences first
+// (exact for nearby values, so a bulk phase's Laplacian carries no
+// cancellation error); FP64 needs no such care and uses fewer operations.
 template <typename Real>
 __device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s, Real ne, Real nw,
-                                         Real se, Real sw, Real& dx, Real& dy, Real& lap)
+                                         Real se, Real sw, Real& dx, Real& dy, Real& lap);
+template <>
+__device__ __forceinline__ void stencils<float>(float c, float e, float w, float n, float s,
+                                                float ne, float nw, float se, float sw, float& dx,
+                                                float& dy, float& lap)
 {
-    stencils_diff<Real>(e - c, w - c, n - c, s - c, ne - c, nw - c, se - c, sw - c, dx, dy, lap);
+    stencils_diff<float>(e - c, w - c, n - c, s - c, ne - c, nw - c, se - c, sw - c, dx, dy, lap);
+}
+template <>
+__device__ __forceinline__ void stencils<double>(double c, double e, double w, double n, double s,
+                                                 double ne, double nw, double se, double sw,
+                                                 double& dx, double& dy, double& lap)
+{
+    dx = div_const<12>(4.0 * (e - w) + (ne - nw) + (se - sw));
+    dy = div_const<12>(4.0 * (n - s) + (ne - se) + (nw - sw));
+    lap = div_const<6>(4.0 * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - 20.0 * c);
 }
 
 // Equilibria of Appendix A (Eq. equilibrium) for i = 1..8, f in deviation
@@ -146,10 +161,14 @@ __device__ __forceinline__ void stencils(Real c, Real e, Real w, Real n, Real s,
 // Written as 36 fe_i and 12 ge_i, whose coefficients (the weights w_i,
 // w^xx, w^yy, w^xy and the 3/2 of the velocity terms, times 36 or 12) are
 // exact, followed by one unbiased division each.
+// m7eq / m8eq receive the two stress moments of f^eq (rows 7, 8 of Eq.
+// Matrix): (fe1 + fe2) - (fe3 + fe4) = rho(ux^2 - uy^2) + kappa(dx^2 - dy^2) and
+// (fe5 + fe6) - (fe7 + fe8) = rho ux uy + kappa dx dy.
 template <typename Real>
 __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
                                            Real jxe, Real jye, Real uxe, Real uye, Real dx,
-                                           Real dy, Real lap, Real (&fe)[9], Real (&ge)[9])
+                                           Real dy, Real lap, Real (&fe)[9], Real (&ge)[9],
+                                           Real& m7eq, Real& m8eq)
 {
     const Real phi2 = phi * phi;
     // 3 x isotropic part: 3 [p0 - kappa phi lap] - rho (Eq. p0 minus the rest pressure)
@@ -161,6 +180,8 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
     // kappa d_a phi d_b phi
     const Real kxx = P.kappa * dx * dx, kyy = P.kappa * dy * dy, kxy = P.kappa * dx * dy;
     const Real ksum = kxx + kyy;
+    m7eq = (rxx - ryy) + (kxx - kyy);
+    m8eq = rxy + kxy;
     // 36 fe_i = even part + odd (momentum) part
     const Real Bx = Real(4) * A3 + Real(18) * rxx - Real(6) * ruu + Real(12) * kxx - Real(6) * kyy;
     const Real By = Real(4) * A3 + Real(18) * ryy - Real(6) * ruu - Real(6) * kxx + Real(12) * kyy;
@@ -219,8 +240,8 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
     const Real jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
     const Real rho = Real(1) + drho;
     const Real irho = rcp_rn(rho);
-    // Eq. (tau)
-    const Real omega = rcp_rn(P.tau_c0 + P.tau_c1 * phi);
+    // Eq. (tau); equal phase viscosities give a constant rate
+    const Real omega = P.tau_c1 == Real(0) ? rcp_rn(P.tau_c0) : rcp_rn(P.tau_c0 + P.tau_c1 * phi);
     // Step 2
     Real jxe = jx, jye = jy, uxe = jx * irho, uye = jy * irho;
     if (step2) {
@@ -229,12 +250,12 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         uxe = Real(0);
         uye = Real(0);
     }
-    Real fe[9], ge[9];
-    equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, ge);
+    Real fe[9], ge[9], m7eq, m8eq;
+    equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, ge, m7eq, m8eq);
     // Step 3
     if (MRT) {
-        const Real m7 = ((f[1] - fe[1]) + (f[2] - fe[2])) - ((f[3] - fe[3]) + (f[4] - fe[4]));
-        const Real m8 = ((f[5] - fe[5]) + (f[6] - fe[6])) - ((f[7] - fe[7]) + (f[8] - fe[8]));
+        const Real m7 = ((f[1] + f[2]) - (f[3] + f[4])) - m7eq;
+        const Real m8 = ((f[5] + f[6]) - (f[7] + f[8])) - m8eq;
         const Real s = (Real(1) - omega) * Real(0.25);
         const Real c7 = s * m7, c8 = s * m8;
         const Real cx = div_const<6>(jx - jxe), cy = div_const<6>(jy - jye);
@@ -252,10 +273,15 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         for (int i = 1; i < 9; ++i) fo[i] = fe[i] + k * (f[i] - fe[i]);
     }
     fo[0] = drho - ((((fo[1] + fo[2]) + (fo[3] + fo[4])) + ((fo[5] + fo[6]) + (fo[7] + fo[8]))));
-    // Eq. (gevo)
-    const Real kg = Real(1) - P.omega_phi;
+    // Eq. (gevo); tau_phi = 1 (Sec. III.B) leaves g' = g^eq
+    if (P.omega_phi == Real(1)) {
 #pragma unroll
-    for (int i = 1; i < 9; ++i) go[i] = ge[i] + kg * (g[i] - ge[i]);
+        for (int i = 1; i < 9; ++i) go[i] = ge[i];
+    } else {
+        const Real kg = Real(1) - P.omega_phi;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) go[i] = ge[i] + kg * (g[i] - ge[i]);
+    }
     go[0] = G0<Real>::advance(g[0], g_tail_sum<Real>(g) - g_tail_sum<Real>(go));
 }
 
