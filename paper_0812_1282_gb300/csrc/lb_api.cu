@@ -66,7 +66,8 @@ int pitch_for(int nx, int precision)
 struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
-    size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0;
+    size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0,
+           sched = 0;
     size_t total = 0;
     long long item_cap = 0;
     int pts_cap = 0;
@@ -112,6 +113,8 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
     off = align_up(off + sizeof(int), kAlign);
     L.err = off;
     off = align_up(off + sizeof(unsigned), kAlign);
+    L.sched = off;
+    off = align_up(off + 2 * sizeof(int), kAlign);
     L.staging = off;
     off = align_up(off + sizeof(double) * 4 * L.staging_nodes, kAlign);
     L.total = off;
@@ -176,6 +179,7 @@ struct lb_handle {
     int* d_count() const { return reinterpret_cast<int*>(base + L.count); }
     double* d_staging() const { return reinterpret_cast<double*>(base + L.staging); }
     unsigned* d_err() const { return reinterpret_cast<unsigned*>(base + L.err); }
+    int* d_sched() const { return reinterpret_cast<int*>(base + L.sched); }
     size_t elem() const { return precision == LB_FP32 ? 4 : 8; }
 };
 
@@ -221,7 +225,8 @@ int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
 {
     const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
                                     h->n_dom > 1 ? h->d_items() : nullptr, h->n_items, h->n_dom,
-                                    parity, h->block_x, h->rows, h->grid_persistent, s);
+                                    parity, h->block_x, h->rows, h->grid_persistent, h->d_sched(),
+                                    s);
     if (e != 0)
         return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
     return LB_OK;

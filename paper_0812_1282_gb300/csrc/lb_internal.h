@@ -49,9 +49,10 @@ constexpr int kStatsFields = 6;
 
 // Launchers implemented in the .cu files.  All return a cudaError_t value
 // cast to int (0 = success) and enqueue on `stream`.
+// sched: two device ints, zero between launches (batched form only).
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x,
-                int rows, int grid_persistent, void* stream);
+                int rows, int grid_persistent, int* sched, void* stream);
 
 int launch_init_phi_drop(int precision, const DomDesc& d, double* phi0, double R, double cx,
                          double cy, void* stream);

@@ -120,7 +120,8 @@ struct TileRows {
 // issued so far (it continues across tiles of a persistent CTA).
 template <typename Real, int S>
 __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             unsigned char* __restrict__ smem, int NW, unsigned& q)
+                                             unsigned char* __restrict__ smem, int NW, unsigned& q,
+                                             int* tags = nullptr, int tag = 0)
 {
     const Real* __restrict__ fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
     const Real* __restrict__ gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
@@ -150,6 +151,9 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
         // rows y0-1 and y1 serve only the phi look-ahead: g segments only
         const bool g_only = (p == 0 && T.first < y0) || (p == T.count() - 1 && T.last >= T.y1);
         if (lane == 0) {
+            // a persistent CTA names the tile in the slot of its first stage;
+            // the arrive below (release) publishes it to the compute warps
+            if (tags && p == 0) tags[slot] = tag;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + slot, (g_only ? 9u : 18u) * segbytes);
         }
@@ -260,8 +264,7 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
         wait_full(1);
         if (active) {
             publish(1, 1, 1);
-            __syncwarp();
-            ghost_row(-1, 1, Real(2) * prm.h_bot);
+            ghost_row(-1, 1, Real(2) * prm.h_bot);  // each lane mirrors its own entries
         }
     }
     bool have_next = bottom_ghost;
@@ -321,6 +324,36 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
     }
     // the last staged row (look-ahead only) is released here
     if (T.last >= y1 && !(walls && y1 == ny)) release(T.count() - 1);
+}
+
+// Producer: the work list is exhausted; complete the next stage slot with
+// no bytes and the tag -1, which tells the compute warps to stop.
+template <typename Real, int S>
+__device__ __forceinline__ void produce_end(unsigned char* smem, int NW, unsigned& q, int* tags,
+                                            unsigned* err)
+{
+    const StageLayout<Real> L(NW, S);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
+    const unsigned slot = q % unsigned(S), use = q / unsigned(S);
+    if (use > 0) mbar_wait(empty + slot, (use - 1) & 1u, err);
+    if ((threadIdx.x & 31) == 0) {
+        tags[slot] = -1;
+        mbar_arrive(full + slot);
+    }
+    __syncwarp();
+    ++q;
+}
+
+// Compute warps: wait for the first stage of the next tile and read its tag.
+template <typename Real, int S>
+__device__ __forceinline__ int next_tag(unsigned char* smem, int NW, unsigned q, const int* tags,
+                                        unsigned* err)
+{
+    const StageLayout<Real> L(NW, S);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
+    if (!mbar_wait(full + (q % unsigned(S)), (q / unsigned(S)) & 1u, err)) return -1;
+    return *reinterpret_cast<const volatile int*>(tags + (q % unsigned(S)));
 }
 
 template <typename Real, int S>

@@ -1,0 +1,71 @@
+"""The 200x100 sessile-drop sweep (BGK and MRT, viscosity ratio 1 and 10,
+target angles 60, 90 and 120 degrees, 20000 steps) on the GPU in FP32 and
+FP64 against the FP64 oracle's stored results (tests/golden/sweep_200x100.json,
+written by tests/golden/make_sweep_200x100.py, which calls only the oracle).
+
+Bars: contact angle within 0.5 degrees (FP32) and 1e-6 degrees (FP64); the
+spurious-current norm max |u| reported and within 2 % (FP32)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbinputs
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sweep_200x100.json")
+
+
+@pytest.fixture(scope="module")
+def lbf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0812_1282_gb300 as m
+
+    return m
+
+
+def _cases():
+    with open(GOLDEN) as fh:
+        return json.load(fh)["cases"]
+
+
+def _run(lbf, case, precision):
+    c = lbinputs.SWEEP_200x100
+    p = lbf.params(**lbinputs.BASE, precision=precision, collision=case["collision"],
+                   tau_alpha=case["tau_alpha"], tau_beta=case["tau_beta"], h_bottom=case["h"],
+                   h_top=0.0)
+    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim.init_drop(c["R"], c["cx"], c["cy"])
+    sim.step(c["steps"])
+    _, _, ux, uy, st = sim.moments()
+    th = sim.contact_angle()[0]
+    sim.close()
+    return th, float(np.hypot(ux, uy).max()), st
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: "%s-R%d-%g" % (c["collision"], c["ratio"],
+                                                                         c["theta_target"]))
+def test_sweep_fp32_angle_within_half_degree(lbf, case):
+    th, umax, st = _run(lbf, case, "fp32")
+    print("%s ratio %d target %.0f: oracle %.4f  gpu-fp32 %.4f  max|u| oracle %.3e gpu %.3e"
+          % (case["collision"], case["ratio"], case["theta_target"], case["theta"], th,
+             case["max_u"], umax))
+    assert abs(th - case["theta"]) <= 0.5
+    assert umax == pytest.approx(case["max_u"], rel=0.02)
+    assert st["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("case", [c for c in _cases() if c["theta_target"] == 120.0],
+                         ids=lambda c: "%s-R%d" % (c["collision"], c["ratio"]))
+def test_sweep_fp64_matches_oracle(lbf, case):
+    th, umax, st = _run(lbf, case, "fp64")
+    assert abs(th - case["theta"]) <= 1e-6
+    assert umax == pytest.approx(case["max_u"], rel=1e-9)
+    assert st["mass"] == pytest.approx(case["mass"], rel=1e-12)
