@@ -69,6 +69,9 @@ typedef struct lb_params {
     int zero_u_at_walls; /* Step 2 of Sec. V: equilibrium velocity 0 on wall rows          */
     int precision;       /* LB_FP32 or LB_FP64                                            */
     int walls;           /* 1: bounce-back walls in y; 0: periodic y                      */
+    int step2_relax_momentum; /* MRT only: on Step-2 rows the momentum rows of Eq. (diag)
+                                 relax at rate 1 (wall-row momentum set to zero) instead of
+                                 the literal rate 0 of the conserved moments (default 0) */
 } lb_params;
 
 /* Diagnostics of one domain (sums over all nodes, in FP64). */

@@ -11,9 +11,10 @@ stated; x periodic; bounce-back walls at y = 0 and y = ny - 1):
 
   DROP_100x50      BGK, tau = 1, neutral walls, drop R = 20 centred on the
                    bottom wall plane; 2000 steps (FP64 parity case).
-  SWEEP_200x100    BGK and MRT, drop R = 40; viscosity ratio 1
-                   (tau 1 / 1) and 10 (tau_alpha 1.5 drop, tau_beta 0.6
-                   gas); target angles 60, 90, 120 degrees; 20000 steps.
+  SWEEP_200x100    BGK and MRT (both readings of the Step-2 momentum
+                   rates), drop R = 40; viscosity ratio 1 (tau 1 / 1) and
+                   10 (tau_alpha 1.5 drop, tau_beta 0.6 gas); target
+                   angles 60, 90, 120 degrees; 20000 steps.
   SPINODAL_8192    MRT, tau_alpha 1.5, tau_beta 0.6, neutral walls,
                    phi uniform in [-0.1, 0.1) from SplitMix64 seed 12345
                    (node (x, y) takes draw y*nx + x); FP32 and FP64.
@@ -79,7 +80,9 @@ DROP_100x50 = dict(nx=100, ny=50, R=20.0, cx=50.0, cy=-0.5, steps=2000,
 SWEEP_200x100 = dict(nx=200, ny=100, R=40.0, cx=100.0, cy=-0.5, steps=20000,
                      angles=(60.0, 90.0, 120.0),
                      tau_pairs={1: (1.0, 1.0), 10: (1.5, 0.6)},
-                     collisions=("bgk", "mrt"))
+                     # (collision, step2_relax_momentum)
+                     variants=(("bgk", False), ("mrt", False), ("mrt", True)),
+                     check_every=500)
 
 SPINODAL_8192 = dict(nx=8192, ny=8192, amp=0.1, seed=12345, steps=1000,
                      sub=512,

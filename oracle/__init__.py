@@ -62,12 +62,14 @@ class OrcParams(ctypes.Structure):
         ("h_bottom", ctypes.c_double), ("h_top", ctypes.c_double),
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("walls", ctypes.c_int), ("mrt_all_rates", ctypes.c_int),
+        ("step2_relax_momentum", ctypes.c_int),
     ]
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
            tau_beta=1.0, h_bottom=0.0, h_top=0.0, collision="bgk",
-           zero_u_at_walls=None, walls=True, mrt_all_rates=False) -> OrcParams:
+           zero_u_at_walls=None, walls=True, mrt_all_rates=False,
+           step2_relax_momentum=False) -> OrcParams:
     """Parameter block.  ``zero_u_at_walls`` defaults to on for MRT (the
     proposed algorithm of Sec. V) and off for BGK."""
     coll = {"bgk": 0, "mrt": 1}[collision] if isinstance(collision, str) else int(collision)
@@ -75,7 +77,7 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
         zero_u_at_walls = coll == 1
     return OrcParams(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom,
                      h_top, coll, int(bool(zero_u_at_walls)), int(bool(walls)),
-                     int(bool(mrt_all_rates)))
+                     int(bool(mrt_all_rates)), int(bool(step2_relax_momentum)))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -99,7 +101,7 @@ def lib():
                 "orc_get_threads": (i, []),
                 "orc_mrt_matrix": (None, [_D, _D]),
                 "orc_node_equilibrium": (None, [P, d, d, d, d, d, d, d, _D, _D]),
-                "orc_node_collide_f": (None, [P, _D, _D, d, _D]),
+                "orc_node_collide_f": (None, [P, _D, _D, d, i, _D]),
                 "orc_phi_derivatives": (None, [P, i, i, _D, _D, _D, _D]),
                 "orc_phi_drop": (None, [P, i, i, d, d, d, _D]),
                 "orc_splitmix64": (u64, [u64, u64]),
@@ -141,11 +143,14 @@ def node_equilibrium(p: OrcParams, rho, phi, ux, uy, dphix, dphiy, lap):
     return feq, geq
 
 
-def node_collide_f(p: OrcParams, f, feq, omega):
+def node_collide_f(p: OrcParams, f, feq, omega, step2_node=False):
+    """Collision of one node; step2_node marks a Step-2 boundary node (it
+    matters only for MRT with step2_relax_momentum)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     feq = np.ascontiguousarray(feq, dtype=np.float64)
     out = np.zeros(9)
-    lib().orc_node_collide_f(ctypes.byref(p), _ptr(f), _ptr(feq), float(omega), _ptr(out))
+    lib().orc_node_collide_f(ctypes.byref(p), _ptr(f), _ptr(feq), float(omega),
+                             int(bool(step2_node)), _ptr(out))
     return out
 
 

@@ -35,7 +35,8 @@
  *    which makes the isotropic y-derivative at the boundary row equal to the
  *    imposed inward gradient exactly;
  *  - boundary nodes of Step 2 are the fluid rows adjacent to a wall;
- *  - conserved-moment rates are the literal zeros of Eq. diag.
+ *  - conserved-moment rates are the literal zeros of Eq. diag (optionally,
+ *    step2_relax_momentum: rate 1 for the momentum rows on Step-2 nodes).
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +58,8 @@ typedef struct orc_params {
     int zero_u_at_walls;      /* Step 2 of Sec. V                           */
     int walls;                /* 1 = walls at y=0 and y=ny-1, 0 = periodic  */
     int mrt_all_rates;        /* test mode: every S entry equal to omega    */
+    int step2_relax_momentum; /* MRT: momentum rows relax at rate 1 on Step-2
+                                 nodes (default 0: the literal zeros of Eq. diag) */
 } orc_params;
 
 /* ---------------------------------------------------------------- lattice */
@@ -166,15 +169,21 @@ void orc_node_equilibrium(const orc_params* p, double rho, double phi,
 }
 
 /* Collision of one node's f (Eq. latbolt or Eq. mrtlb) given its
- * equilibrium, omega = 1/tau_rho and the inverse moment matrix. */
+ * equilibrium, omega = 1/tau_rho and the inverse moment matrix.
+ * step2_node: the node is a Step-2 boundary node (only matters for MRT
+ * with step2_relax_momentum set). */
 static void collide_f(const orc_params* p, const double minv[9][9], const double* f,
-                      const double* feq, double omega, double* fout)
+                      const double* feq, double omega, int step2_node, double* fout)
 {
     if (p->collision == 0) {
         for (int i = 0; i < 9; ++i) fout[i] = f[i] - omega * (f[i] - feq[i]);
         return;
     }
     double s[9] = {0.0, 1.0, 1.0, 0.0, 1.0, 0.0, 1.0, omega, omega}; /* Eq. diag */
+    if (step2_node && p->step2_relax_momentum) {
+        s[3] = 1.0; /* alternative reading: the momentum of a Step-2 node */
+        s[5] = 1.0; /* relaxes to its zero-velocity equilibrium           */
+    }
     if (p->mrt_all_rates)
         for (int k = 0; k < 9; ++k) s[k] = omega;
     double m[9];
@@ -191,11 +200,11 @@ static void collide_f(const orc_params* p, const double minv[9][9], const double
 }
 
 void orc_node_collide_f(const orc_params* p, const double* f, const double* feq,
-                        double omega, double* fout)
+                        double omega, int step2_node, double* fout)
 {
     double minv[9][9];
     mrt_inverse(minv);
-    collide_f(p, minv, f, feq, omega, fout);
+    collide_f(p, minv, f, feq, omega, step2_node, fout);
 }
 
 /* ------------------------------------------------------ phi derivatives */
@@ -375,7 +384,8 @@ void orc_step(const orc_params* p, int nx, int ny, double* f, double* g, int nst
             for (int x = 0; x < nx; ++x) {
                 const size_t kk = (size_t)y * nx + x;
                 double ueqx = ux[kk], ueqy = uy[kk];
-                if (p->zero_u_at_walls && is_boundary_node(p, ny, y)) {
+                const int step2_node = p->zero_u_at_walls && is_boundary_node(p, ny, y);
+                if (step2_node) {
                     ueqx = 0.0;
                     ueqy = 0.0;
                 }
@@ -387,7 +397,7 @@ void orc_step(const orc_params* p, int nx, int ny, double* f, double* g, int nst
                                    0.5 * (phi[kk] + 1.0) * (p->tau_alpha - p->tau_beta);
                 const double omega = 1.0 / tau;
                 for (int i = 0; i < 9; ++i) fin[i] = fs[(size_t)i * n + kk];
-                collide_f(p, minv, fin, feq, omega, fout);
+                collide_f(p, minv, fin, feq, omega, step2_node, fout);
                 for (int i = 0; i < 9; ++i) {
                     f[(size_t)i * n + kk] = fout[i];
                     const double gi = gs[(size_t)i * n + kk];
@@ -521,14 +531,15 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
             }
             const double ph = phi_full[kk];
             double ueqx = jx / r, ueqy = jy / r;
-            if (p->zero_u_at_walls && is_boundary_node(p, ny, y)) {
+            const int step2_node = p->zero_u_at_walls && is_boundary_node(p, ny, y);
+            if (step2_node) {
                 ueqx = 0.0;
                 ueqy = 0.0;
             }
             double feq[9], geq[9], fo[9];
             orc_node_equilibrium(p, r, ph, ueqx, ueqy, dxv, dyv, lapv, feq, geq);
             const double tau = p->tau_beta + 0.5 * (ph + 1.0) * (p->tau_alpha - p->tau_beta);
-            collide_f(p, minv, fin, feq, 1.0 / tau, fo);
+            collide_f(p, minv, fin, feq, 1.0 / tau, step2_node, fo);
             const size_t wk = (size_t)(y - y0) * wx + (x - x0);
             for (int i = 0; i < 9; ++i) {
                 fout_w[(size_t)i * wx * wy + wk] = fo[i];

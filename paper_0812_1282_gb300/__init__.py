@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("h_bottom", ctypes.c_double), ("h_top", ctypes.c_double),
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("precision", ctypes.c_int), ("walls", ctypes.c_int),
+        ("step2_relax_momentum", ctypes.c_int),
     ]
 
 
@@ -72,16 +73,18 @@ class Stats(ctypes.Structure):
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,
            h_bottom=0.0, h_top=0.0, collision="bgk", zero_u_at_walls=None,
-           precision="fp64", walls=True) -> Params:
+           precision="fp64", walls=True, step2_relax_momentum=False) -> Params:
     """Parameter block (lattice units).  Step 2 of the proposed algorithm
     (zero equilibrium velocity on wall rows) defaults to on for MRT and off
-    for BGK."""
+    for BGK; step2_relax_momentum selects the alternative reading of the
+    momentum rates on those rows (see include/lbfe.h)."""
     coll = {"bgk": LB_BGK, "mrt": LB_MRT}[collision] if isinstance(collision, str) else int(collision)
     prec = {"fp32": LB_FP32, "fp64": LB_FP64}[precision] if isinstance(precision, str) else int(precision)
     if zero_u_at_walls is None:
         zero_u_at_walls = coll == LB_MRT
     return Params(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom, h_top, coll,
-                  int(bool(zero_u_at_walls)), prec, int(bool(walls)))
+                  int(bool(zero_u_at_walls)), prec, int(bool(walls)),
+                  int(bool(step2_relax_momentum)))
 
 
 _lib = None

@@ -144,6 +144,8 @@ int validate(const lb_params* p)
     if (p->precision != LB_FP32 && p->precision != LB_FP64)
         return fail(LB_ERR_INVALID_ARG, "precision must be LB_FP32 or LB_FP64");
     if (p->walls != 0 && p->walls != 1) return fail(LB_ERR_INVALID_ARG, "walls must be 0 or 1");
+    if (p->step2_relax_momentum != 0 && p->step2_relax_momentum != 1)
+        return fail(LB_ERR_INVALID_ARG, "step2_relax_momentum must be 0 or 1");
     return LB_OK;
 }
 
@@ -391,6 +393,7 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         }
         D.walls = p.walls;
         D.step2 = p.zero_u_at_walls ? 1 : 0;
+        D.step2_relax_j = p.step2_relax_momentum ? 1 : 0;
         D.a = p.a;
         D.kappa = p.kappa;
         D.gamma = p.gamma_mob;

@@ -22,7 +22,7 @@ struct DomDesc {
     int nx, ny, pitch;
     int walls;         // 1: bounce-back walls below row 0 and above row ny-1
     int step2;         // zero equilibrium velocity on wall rows (Sec. V, Step 2)
-    int pad_;
+    int step2_relax_j; // MRT: relax wall-row momentum at rate 1 (alternative reading)
     double a, kappa, gamma;   // free energy and mobility parameters
     double omega_phi;         // 1 / tau_phi
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)

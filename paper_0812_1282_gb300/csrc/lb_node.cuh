@@ -228,11 +228,14 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
 // rows (rate 0; non-zero only where Step 2 zeroes u_eq) and the two stress
 // rows (rate w) survive, so
 //   f'_i = f^eq_i + M_3i dj_x/6 + M_5i dj_y/6 + (1-w)(M_7i m_7 + M_8i m_8)/4,
-// with m_7 = d1+d2-d3-d4, m_8 = d5+d6-d7-d8, d = f - f^eq.
+// with m_7 = d1+d2-d3-d4, m_8 = d5+d6-d7-d8, d = f - f^eq.  With
+// step2_relax_j the momentum rows of a Step-2 node relax at rate 1 instead
+// (the dj terms vanish and the node leaves the collision at rest).
 template <typename Real, bool MRT>
 __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&f)[9],
                                         const Real (&g)[9], Real phi, Real dx, Real dy, Real lap,
-                                        bool step2, Real (&fo)[9], Real (&go)[9])
+                                        bool step2, bool step2_relax_j, Real (&fo)[9],
+                                        Real (&go)[9])
 {
     // Step 1 (Eq. moments); t_i e_i sums to zero, so deviations give j directly
     const Real drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
@@ -258,7 +261,11 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         const Real m8 = ((f[5] + f[6]) - (f[7] + f[8])) - m8eq;
         const Real s = (Real(1) - omega) * Real(0.25);
         const Real c7 = s * m7, c8 = s * m8;
-        const Real cx = div_const<6>(jx - jxe), cy = div_const<6>(jy - jye);
+        // momentum rows: rate 0 (literal Eq. diag) keeps j - j^eq; the alternative
+        // reading relaxes it fully on Step-2 rows
+        const bool keep_j = !(step2 && step2_relax_j);
+        const Real cx = keep_j ? div_const<6>(jx - jxe) : Real(0);
+        const Real cy = keep_j ? div_const<6>(jy - jye) : Real(0);
         fo[1] = fe[1] + c7 + cx;
         fo[2] = fe[2] + c7 - cx;
         fo[3] = fe[3] - c7 + cy;

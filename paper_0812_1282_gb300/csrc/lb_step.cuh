@@ -296,7 +296,7 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
                            sp[own - 1], sm[own + 1], sm[own - 1], dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
             Real fo[9], go[9];
-            collide<Real, MRT>(prm, f, g, c, dx, dy, lap, s2, fo, go);
+            collide<Real, MRT>(prm, f, g, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, go);
             const int o = y * pitch + x + kXOff;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {

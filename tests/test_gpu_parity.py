@@ -94,10 +94,12 @@ def test_fp64_bgk_drop_100x50_2000_steps(lbf, orc):
     assert st["step"] == c["steps"]
 
 
-@pytest.mark.parametrize("coll,step2", [("mrt", True), ("mrt", False), ("bgk", True)])
-def test_fp64_viscosity_ratio_wetting(lbf, orc, coll, step2):
+@pytest.mark.parametrize("coll,step2,relax", [("mrt", True, False), ("mrt", False, False),
+                                              ("bgk", True, False), ("mrt", True, True)])
+def test_fp64_viscosity_ratio_wetting(lbf, orc, coll, step2, relax):
     kw = dict(collision=coll, zero_u_at_walls=step2, tau_alpha=3.0, tau_beta=0.7,
-              h_bottom=orc.wetting_h(60.0), h_top=orc.wetting_h(110.0), gamma_mob=0.5)
+              h_bottom=orc.wetting_h(60.0), h_top=orc.wetting_h(110.0), gamma_mob=0.5,
+              step2_relax_momentum=relax)
     sim, ref = make_pair(lbf, orc, 96, 40, "fp64", **kw)
     sim.init_drop(18.0, 48.0, -0.5)
     ref.init_drop(18.0, 48.0, -0.5)
@@ -128,15 +130,16 @@ def _random_flow_state(orc, p, nx, ny, seed):
     return f + noise[0], g + noise[1]
 
 
-@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+@pytest.mark.parametrize("coll,relax", [("bgk", False), ("mrt", False), ("mrt", True)])
 @pytest.mark.parametrize("walls", [True, False])
-def test_fp64_random_flow_states(lbf, orc, coll, walls):
+def test_fp64_random_flow_states(lbf, orc, coll, relax, walls):
     """Arbitrary states with flow (every velocity term of the equilibria,
-    Step 2 with u != 0, bounce-back of non-equilibrium populations): a few
-    steps from the same populations agree to 1e-13."""
+    Step 2 with u != 0 under both readings of the momentum rates, bounce-back
+    of non-equilibrium populations): a few steps from the same populations
+    agree to 1e-13."""
     nx, ny = 41, 23
     kw = dict(collision=coll, tau_alpha=1.7, tau_beta=0.65, tau_phi=0.9, walls=walls,
-              h_bottom=0.13, h_top=-0.21, gamma_mob=0.3)
+              h_bottom=0.13, h_top=-0.21, gamma_mob=0.3, step2_relax_momentum=relax)
     sim, ref = make_pair(lbf, orc, nx, ny, "fp64", **kw)
     f, g = _random_flow_state(orc, ref.p, nx, ny, 7)
     ref.f[:] = f
@@ -193,13 +196,15 @@ def test_fp32_tile_independence(lbf):
 
 
 # ---------------------------------------------------------- FP32
-@pytest.mark.parametrize("coll,taus", [("bgk", (1.0, 1.0)), ("mrt", (1.5, 0.6)),
-                                       ("bgk", (1.5, 0.6))])
+@pytest.mark.parametrize("coll,taus,relax", [("bgk", (1.0, 1.0), False),
+                                             ("mrt", (1.5, 0.6), False),
+                                             ("bgk", (1.5, 0.6), False),
+                                             ("mrt", (1.5, 0.6), True)])
 @pytest.mark.parametrize("theta", [60.0, 120.0])
-def test_fp32_phi_within_1e5_after_1000_steps(lbf, orc, coll, taus, theta):
+def test_fp32_phi_within_1e5_after_1000_steps(lbf, orc, coll, taus, relax, theta):
     c = lbinputs.SWEEP_200x100
     kw = dict(lbinputs.BASE, collision=coll, tau_alpha=taus[0], tau_beta=taus[1],
-              h_bottom=orc.wetting_h(theta), h_top=0.0)
+              h_bottom=orc.wetting_h(theta), h_top=0.0, step2_relax_momentum=relax)
     sim, ref = make_pair(lbf, orc, c["nx"], c["ny"], "fp32", **kw)
     sim.init_drop(c["R"], c["cx"], c["cy"])
     ref.init_drop(c["R"], c["cx"], c["cy"])

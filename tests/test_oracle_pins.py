@@ -157,6 +157,41 @@ def test_step2_boundary_collision_moments(oracle_mod):
                 assert np.allclose(jo, (1 - omega) * j, atol=1e-15)
 
 
+def test_step2_relax_momentum_reading(oracle_mod):
+    """Alternative reading of Eq. (diag) on Step-2 nodes: the two momentum
+    rows relax at rate 1, so the node leaves the collision with zero momentum
+    (the no-slip condition Step 2 is said to express), while rho is conserved
+    and the non-conserved moments are exactly those of the literal reading.
+    Away from Step-2 nodes the flag changes nothing."""
+    rng = np.random.default_rng(31)
+    M, _ = oracle_mod.mrt_matrix()
+    lit = oracle_mod.params(collision="mrt")
+    alt = oracle_mod.params(collision="mrt", step2_relax_momentum=True)
+    for _ in range(20):
+        rho = 1.0 + 0.01 * rng.standard_normal()
+        phi = rng.uniform(-1, 1)
+        u = 0.02 * rng.standard_normal(2)
+        d = 0.2 * rng.standard_normal(3)
+        feq_true, _ = oracle_mod.node_equilibrium(lit, rho, phi, u[0], u[1], *d)
+        feq0, _ = oracle_mod.node_equilibrium(lit, rho, phi, 0.0, 0.0, *d)
+        f = feq_true + 1e-3 * rng.standard_normal(9)
+        m = M @ f
+        m[[0, 3, 5]] = (M @ feq_true)[[0, 3, 5]]
+        f = np.linalg.solve(M, m)
+        omega = rng.uniform(0.5, 1.8)
+        fl = oracle_mod.node_collide_f(lit, f, feq0, omega, step2_node=True)
+        fa = oracle_mod.node_collide_f(alt, f, feq0, omega, step2_node=True)
+        ml, ma = M @ fl, M @ fa
+        assert abs(ma[0] - rho) < 1e-14
+        assert np.allclose(ma[[3, 5]], 0.0, atol=1e-16)
+        assert np.allclose(ml[[3, 5]], (M @ f)[[3, 5]], atol=1e-15)
+        keep = [0, 1, 2, 4, 6, 7, 8]
+        assert np.allclose(ma[keep], ml[keep], atol=1e-15)
+        # interior node: identical
+        fi = oracle_mod.node_collide_f(alt, f, feq_true, omega, step2_node=False)
+        assert np.array_equal(fi, oracle_mod.node_collide_f(lit, f, feq_true, omega))
+
+
 # ------------------------------------------------------- equilibria
 def test_equilibrium_moments_reproduce_pressure_tensor(oracle_mod):
     """Appendix A: the equilibria are built so that sum f = rho,
