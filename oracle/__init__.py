@@ -81,11 +81,17 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
 
 
 _D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
 
 
 def _ptr(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(_D)
+
+
+def _ptr8(a: np.ndarray):
+    assert a.dtype == np.uint8 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_U8)
 
 
 def lib():
@@ -110,6 +116,10 @@ def lib():
                 "orc_step": (None, [P, i, i, _D, _D, i]),
                 "orc_moments": (None, [i, i, _D, _D, _D, _D, _D, _D]),
                 "orc_step_window": (i, [P, i, i, i, i, _D, _D, i, i, i, i, _D, _D]),
+                "orc_geo_check": (i, [P, i, i, _U8]),
+                "orc_phi_derivatives_geo": (None, [P, i, i, _U8, _D, _D, _D, _D, _D]),
+                "orc_init_geo": (i, [P, i, i, _U8, _D, _D, _D, _D]),
+                "orc_step_geo": (i, [P, i, i, _U8, _D, _D, _D, i]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -182,7 +192,8 @@ def phi_random(nx, ny, amp, seed):
 
 
 class OracleLattice:
-    """Full lattice state (post-collision f', g') advanced by the oracle."""
+    """Full lattice state (post-collision f', g') advanced by the oracle.
+    With a geometry (``set_geometry``) the lattice holds solid obstacles."""
 
     def __init__(self, p: OrcParams, nx: int, ny: int):
         if nx < 3 or ny < 3:
@@ -192,13 +203,37 @@ class OracleLattice:
         self.f = np.zeros((9, ny, nx))
         self.g = np.zeros((9, ny, nx))
         self.t = 0
+        self.cls = None
+        self.hcls = None
+
+    def set_geometry(self, cls: np.ndarray, hcls) -> None:
+        """cls: (ny, nx) uint8, 0 fluid, k in 1..7 solid of wetting class k;
+        hcls: the wetting gradient of each class (index 0 unused)."""
+        cls = np.ascontiguousarray(cls, dtype=np.uint8)
+        assert cls.shape == (self.ny, self.nx)
+        h = np.zeros(8)
+        h[:len(hcls)] = hcls
+        if lib().orc_geo_check(ctypes.byref(self.p), self.nx, self.ny, _ptr8(cls)) != 0:
+            raise ValueError("geometry rejected (feature thinner than two nodes or bad class)")
+        self.cls, self.hcls = cls, h
 
     def init_phi(self, phi0: np.ndarray) -> None:
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
         assert phi0.shape == (self.ny, self.nx)
-        lib().orc_init(ctypes.byref(self.p), self.nx, self.ny, _ptr(phi0),
-                       _ptr(self.f), _ptr(self.g))
+        if self.cls is None:
+            lib().orc_init(ctypes.byref(self.p), self.nx, self.ny, _ptr(phi0),
+                           _ptr(self.f), _ptr(self.g))
+        else:
+            lib().orc_init_geo(ctypes.byref(self.p), self.nx, self.ny, _ptr8(self.cls),
+                               _ptr(self.hcls), _ptr(phi0), _ptr(self.f), _ptr(self.g))
         self.t = 0
+
+    def init_channel(self, res_len: int, ch_w: int, h_channel: float, h_block: float) -> None:
+        """Capillary filling set-up (Sec. VI): see channel_geometry and
+        channel_phi0."""
+        self.set_geometry(channel_geometry(self.nx, self.ny, res_len, ch_w),
+                          [0.0, h_channel, h_block])
+        self.init_phi(channel_phi0(self.p, self.nx, self.ny, res_len, ch_w))
 
     def init_drop(self, R, cx, cy):
         self.init_phi(phi_drop(self.p, self.nx, self.ny, R, cx, cy))
@@ -207,8 +242,13 @@ class OracleLattice:
         self.init_phi(phi_random(self.nx, self.ny, amp, seed))
 
     def step(self, n: int = 1) -> None:
-        lib().orc_step(ctypes.byref(self.p), self.nx, self.ny, _ptr(self.f),
-                       _ptr(self.g), int(n))
+        if self.cls is None:
+            lib().orc_step(ctypes.byref(self.p), self.nx, self.ny, _ptr(self.f),
+                           _ptr(self.g), int(n))
+        else:
+            rc = lib().orc_step_geo(ctypes.byref(self.p), self.nx, self.ny, _ptr8(self.cls),
+                                    _ptr(self.hcls), _ptr(self.f), _ptr(self.g), int(n))
+            assert rc == 0
         self.t += int(n)
 
     def moments(self):
@@ -328,3 +368,71 @@ def contact_angle(phi: np.ndarray, wall_y: float = -0.5, exclude: float = 2.0):
     xc, yc, R = fit_circle(pts)
     s = max(-1.0, min(1.0, (yc - wall_y) / R))
     return 90.0 + math.degrees(math.asin(s)), R, xc, yc
+
+
+# ------------------------------------------------ capillary filling, Sec. VI
+def channel_geometry(nx: int, ny: int, res_len: int, ch_w: int) -> np.ndarray:
+    """Solid classes of the capillary set-up: the columns x >= res_len are
+    solid except the channel rows [y0, y0 + ch_w), y0 = (ny - ch_w) // 2.
+    Class 1: the two solid rows that bound the channel (its walls); class 2:
+    every other solid node (the block end faces and interiors)."""
+    y0 = (ny - ch_w) // 2
+    cls = np.zeros((ny, nx), dtype=np.uint8)
+    cls[:, res_len:] = 2
+    cls[y0:y0 + ch_w, res_len:] = 0
+    cls[y0 - 1, res_len:] = 1
+    cls[y0 + ch_w, res_len:] = 1
+    return cls
+
+
+def channel_phi0(p: OrcParams, nx: int, ny: int, res_len: int, ch_w: int) -> np.ndarray:
+    """Initial order parameter of the capillary set-up: phase alpha (+1)
+    fills the reservoir columns [res_len // 2, res_len), phase beta (-1) the
+    rest (the other half of the reservoir, which the channel outlet reaches
+    through the periodic x boundary, and the channel).  Flat tanh profiles
+    of width sqrt(2 kappa / a) centred half a node before each interface
+    column; solid nodes carry 0."""
+    l = math.sqrt(2.0 * p.kappa / p.a)
+    xa, xb = res_len // 2, res_len
+    x = np.arange(nx, dtype=np.float64)
+    d = np.minimum(x - (xa - 0.5), (xb - 0.5) - x)
+    phi = np.tile(np.tanh(d / l), (ny, 1))
+    phi[channel_geometry(nx, ny, res_len, ch_w) != 0] = 0.0
+    return phi
+
+
+def meniscus(phi: np.ndarray, cls: np.ndarray, x_lo: int, x_hi: int, y_lo: int, y_hi: int,
+             exclude: float = 2.0):
+    """Meniscus of a channel whose walls are the planes y_lo - 1/2 and
+    y_hi - 1/2, with phase alpha (phi > 0) behind it (smaller x).  The phi = 0
+    crossings on fluid-fluid links inside [x_lo, x_hi) x [y_lo, y_hi),
+    farther than `exclude` from both walls, are fitted with a circle.
+    Returns (x_front, theta_deg, R): x_front is the circle's x on the channel
+    centre line (on the branch facing the points); theta is the angle
+    through alpha at the two walls (mean of both), from the circle."""
+    pts = []
+    for y in range(y_lo, y_hi):
+        for x in range(x_lo, x_hi):
+            if cls[y, x]:
+                continue
+            a = phi[y, x]
+            if x + 1 < x_hi and not cls[y, x + 1]:
+                b = phi[y, x + 1]
+                if (a > 0 > b) or (a < 0 < b):
+                    pts.append((x + a / (a - b), float(y)))
+            if y + 1 < y_hi and not cls[y + 1, x]:
+                c = phi[y + 1, x]
+                if (a > 0 > c) or (a < 0 < c):
+                    pts.append((float(x), y + a / (a - c)))
+    wb, wt = y_lo - 0.5, y_hi - 0.5
+    pts = np.array([q for q in pts if wb + exclude <= q[1] <= wt - exclude])
+    if len(pts) < 3:
+        raise ValueError("fewer than three meniscus points")
+    xc, yc, R = fit_circle(pts)
+    # centre ahead of the points (on the beta side): alpha wets, theta < 90
+    s = 1.0 if xc > pts[:, 0].mean() else -1.0
+    th_b = math.degrees(math.acos(max(-1.0, min(1.0, s * (yc - wb) / R))))
+    th_t = math.degrees(math.acos(max(-1.0, min(1.0, s * (wt - yc) / R))))
+    ym = 0.5 * (wb + wt)
+    x_front = xc - s * math.sqrt(max(R * R - (ym - yc) ** 2, 0.0))
+    return x_front, 0.5 * (th_b + th_t), R

@@ -551,3 +551,268 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
     free(phi_full);
     return 0;
 }
+
+/* ============================================================ geometry */
+/* Solid obstacles inside the lattice (capillary filling, Sec. VI).
+ *
+ * cls[y*nx + x] = 0 marks a fluid node and k in 1..7 a solid node of
+ * wetting class k, whose inward-normal wetting gradient is hcls[k].  With
+ * walls == 1 the rows y = -1 and y = ny are solid as well, with h_bottom and
+ * h_top.  Solid nodes carry no fluid: their populations are never streamed
+ * from or collided.
+ *
+ * Readings (the paper states the wetting condition only for a flat wall):
+ *  - bounce-back: a population whose pull source r - e_i is solid is the
+ *    node's own reversed post-collision population (mid-link, as for walls);
+ *  - Step-2 boundary nodes: fluid nodes with a solid node among their eight
+ *    neighbours;
+ *  - wetting ghost value of a solid node s next to fluid: the mirror rule of
+ *    the flat wall applied along each axis direction d in which s + d is
+ *    fluid, averaged: phi(s) = mean_d phi(s + 2d) - 2 h(s).  If no axis
+ *    neighbour is fluid (s touches fluid through a corner only) the
+ *    diagonal directions are used the same way.  Every mirror node s + 2d
+ *    must be fluid (features at least two nodes thick); otherwise the
+ *    geometry is rejected.
+ * On an obstacle-free lattice this is exactly the ghost-row rule above. */
+static int geo_solid(const orc_params* p, int nx, int ny, const unsigned char* cls, int x, int y)
+{
+    if (p->walls && (y < 0 || y >= ny)) return 1;
+    x = wrap(x, nx);
+    y = wrap(y, ny);
+    return cls[(size_t)y * nx + x] != 0;
+}
+
+static double geo_h(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                    const double* hcls, int x, int y)
+{
+    if (p->walls && y < 0) return p->h_bottom;
+    if (p->walls && y >= ny) return p->h_top;
+    return hcls[cls[(size_t)wrap(y, ny) * nx + wrap(x, nx)]];
+}
+
+/* Mirror directions of solid node (x, y): axis directions with a fluid
+ * neighbour, else diagonal ones.  Returns how many (0: no fluid neighbour). */
+static int geo_mirror_dirs(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                           int x, int y, int dirs[4][2])
+{
+    static const int AX[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    static const int DG[4][2] = {{1, 1}, {-1, -1}, {-1, 1}, {1, -1}};
+    int n = 0;
+    for (int k = 0; k < 4; ++k)
+        if (!geo_solid(p, nx, ny, cls, x + AX[k][0], y + AX[k][1])) {
+            dirs[n][0] = AX[k][0];
+            dirs[n][1] = AX[k][1];
+            ++n;
+        }
+    if (n > 0) return n;
+    for (int k = 0; k < 4; ++k)
+        if (!geo_solid(p, nx, ny, cls, x + DG[k][0], y + DG[k][1])) {
+            dirs[n][0] = DG[k][0];
+            dirs[n][1] = DG[k][1];
+            ++n;
+        }
+    return n;
+}
+
+/* 0 if every solid node next to fluid has fluid mirror nodes, -1 if not,
+ * -2 if a class index is out of range. */
+int orc_geo_check(const orc_params* p, int nx, int ny, const unsigned char* cls)
+{
+    for (int y = -1; y <= ny; ++y) {
+        if (!p->walls && (y < 0 || y >= ny)) continue;
+        for (int x = 0; x < nx; ++x) {
+            if (y >= 0 && y < ny && cls[(size_t)y * nx + x] > 7) return -2;
+            if (!geo_solid(p, nx, ny, cls, x, y)) continue;
+            int dirs[4][2];
+            const int n = geo_mirror_dirs(p, nx, ny, cls, x, y, dirs);
+            for (int k = 0; k < n; ++k)
+                if (geo_solid(p, nx, ny, cls, x + 2 * dirs[k][0], y + 2 * dirs[k][1])) return -1;
+        }
+    }
+    return 0;
+}
+
+/* phi at (x, y), x periodic, y periodic or walled, with the ghost rule at
+ * solid nodes.  Only called for nodes next to fluid. */
+static double geo_phi_at(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                         const double* hcls, const double* phi, int x, int y)
+{
+    if (!geo_solid(p, nx, ny, cls, x, y))
+        return phi[(size_t)wrap(y, ny) * nx + wrap(x, nx)];
+    int dirs[4][2];
+    const int n = geo_mirror_dirs(p, nx, ny, cls, x, y, dirs);
+    double sum = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const int mx = x + 2 * dirs[k][0], my = y + 2 * dirs[k][1];
+        sum += phi[(size_t)wrap(my, ny) * nx + wrap(mx, nx)];
+    }
+    return sum / n - 2.0 * geo_h(p, nx, ny, cls, hcls, x, y);
+}
+
+/* Eq. best at every fluid node with the ghost rule at solid neighbours;
+ * solid nodes get 0. */
+void orc_phi_derivatives_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                             const double* hcls, const double* phi, double* dx, double* dy,
+                             double* lap)
+{
+    int y;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+    for (y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t k = (size_t)y * nx + x;
+            dx[k] = dy[k] = lap[k] = 0.0;
+            if (cls[k] != 0) continue;
+            double sx = 0.0, sy = 0.0, sl = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    const double v = geo_phi_at(p, nx, ny, cls, hcls, phi, x + c - 1, y + r - 1);
+                    sx += DX_STENCIL[r][c] * v;
+                    sy += DX_STENCIL[c][r] * v;
+                    sl += LAP_STENCIL[r][c] * v;
+                }
+            dx[k] = sx / 12.0;
+            dy[k] = sy / 12.0;
+            lap[k] = sl / 6.0;
+        }
+}
+
+/* Initial populations with obstacles: fluid nodes as orc_init (with the
+ * ghost rule), solid nodes at rest with no order parameter (f = w, g = 0). */
+int orc_init_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                 const double* hcls, const double* phi0, double* f, double* g)
+{
+    if (orc_geo_check(p, nx, ny, cls) != 0) return -1;
+    static const double T[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const size_t n = (size_t)nx * ny;
+    double* dx = malloc(n * sizeof(double));
+    double* dy = malloc(n * sizeof(double));
+    double* lap = malloc(n * sizeof(double));
+    orc_phi_derivatives_geo(p, nx, ny, cls, hcls, phi0, dx, dy, lap);
+    for (size_t k = 0; k < n; ++k) {
+        double feq[9], geq[9];
+        if (cls[k] != 0) {
+            for (int i = 0; i < 9; ++i) {
+                feq[i] = T[i];
+                geq[i] = 0.0;
+            }
+        } else {
+            orc_node_equilibrium(p, 1.0, phi0[k], 0.0, 0.0, dx[k], dy[k], lap[k], feq, geq);
+        }
+        for (int i = 0; i < 9; ++i) {
+            f[(size_t)i * n + k] = feq[i];
+            g[(size_t)i * n + k] = geq[i];
+        }
+    }
+    free(dx);
+    free(dy);
+    free(lap);
+    return 0;
+}
+
+/* nsteps time steps with obstacles: Steps 1-4 of Sec. V on the fluid
+ * nodes, with the readings stated above.  Returns -1 (state untouched) if
+ * the geometry is rejected. */
+int orc_step_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
+                 const double* hcls, double* f, double* g, int nsteps)
+{
+    if (orc_geo_check(p, nx, ny, cls) != 0) return -1;
+    const size_t n = (size_t)nx * ny;
+    double* fs = malloc(9 * n * sizeof(double));
+    double* gs = malloc(9 * n * sizeof(double));
+    double* rho = calloc(n, sizeof(double));
+    double* phi = calloc(n, sizeof(double));
+    double* ux = calloc(n, sizeof(double));
+    double* uy = calloc(n, sizeof(double));
+    double* dx = malloc(n * sizeof(double));
+    double* dy = malloc(n * sizeof(double));
+    double* lap = malloc(n * sizeof(double));
+    double minv[9][9];
+    mrt_inverse(minv);
+
+    for (int s = 0; s < nsteps; ++s) {
+        /* pull-stream with bounce-back from solid sources (fluid nodes only) */
+        int y;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+        for (y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t k = (size_t)y * nx + x;
+                if (cls[k] != 0) continue;
+                for (int i = 0; i < 9; ++i) {
+                    const int sx = x - EX[i], sy = y - EY[i];
+                    size_t src;
+                    int pop;
+                    if (geo_solid(p, nx, ny, cls, sx, sy)) {
+                        src = k;
+                        pop = OPP[i];
+                    } else {
+                        src = (size_t)wrap(sy, ny) * nx + wrap(sx, nx);
+                        pop = i;
+                    }
+                    fs[(size_t)i * n + k] = f[(size_t)pop * n + src];
+                    gs[(size_t)i * n + k] = g[(size_t)pop * n + src];
+                }
+            }
+
+        /* Step 1: Eq. moments on fluid nodes */
+        long long k;
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+        for (k = 0; k < (long long)n; ++k) {
+            if (cls[k] != 0) continue;
+            double r = 0.0, ph = 0.0, jx = 0.0, jy = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                const double fi = fs[(size_t)i * n + k];
+                r += fi;
+                jx += fi * EX[i];
+                jy += fi * EY[i];
+                ph += gs[(size_t)i * n + k];
+            }
+            rho[k] = r;
+            phi[k] = ph;
+            ux[k] = jx / r;
+            uy[k] = jy / r;
+        }
+
+        /* Eq. best with the ghost rule at solid neighbours */
+        orc_phi_derivatives_geo(p, nx, ny, cls, hcls, phi, dx, dy, lap);
+
+        /* Step 2, equilibria, Step 3 collision */
+#pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
+        for (y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t kk = (size_t)y * nx + x;
+                if (cls[kk] != 0) continue;
+                int next_to_solid = 0;
+                for (int i = 1; i < 9; ++i)
+                    if (geo_solid(p, nx, ny, cls, x + EX[i], y + EY[i])) next_to_solid = 1;
+                const int step2_node = p->zero_u_at_walls && next_to_solid;
+                double ueqx = ux[kk], ueqy = uy[kk];
+                if (step2_node) {
+                    ueqx = 0.0;
+                    ueqy = 0.0;
+                }
+                double feq[9], geq[9], fin[9], fout[9];
+                orc_node_equilibrium(p, rho[kk], phi[kk], ueqx, ueqy, dx[kk], dy[kk], lap[kk],
+                                     feq, geq);
+                const double tau = p->tau_beta +
+                                   0.5 * (phi[kk] + 1.0) * (p->tau_alpha - p->tau_beta);
+                for (int i = 0; i < 9; ++i) fin[i] = fs[(size_t)i * n + kk];
+                collide_f(p, minv, fin, feq, 1.0 / tau, step2_node, fout);
+                for (int i = 0; i < 9; ++i) {
+                    f[(size_t)i * n + kk] = fout[i];
+                    const double gi = gs[(size_t)i * n + kk];
+                    g[(size_t)i * n + kk] = gi - (gi - geq[i]) / p->tau_phi; /* Eq. gevo */
+                }
+            }
+    }
+    free(fs);
+    free(gs);
+    free(rho);
+    free(phi);
+    free(ux);
+    free(uy);
+    free(dx);
+    free(dy);
+    free(lap);
+    return 0;
+}
