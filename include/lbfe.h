@@ -157,6 +157,60 @@ int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi,
 int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
                      double* R, double* xc, double* yc);
 
+/* Solid obstacles in domain dom (the capillary geometry of Sec. VI; the
+ * paper states bounce-back and the wetting condition for flat walls only,
+ * and they are read here node by node).
+ *  cls:     host array [ny][nx]; 0 marks a fluid node, k in 1..7 a solid node
+ *           of wetting class k.  NULL removes the obstacles.  Copied before
+ *           the call returns.
+ *  h_class: n_class (1..8) inward-normal wetting gradients, h_class[k] for
+ *           class k (entry 0 unused).
+ * Rules: a pull from a solid node is bounced back (mid-link, as at a wall);
+ * Step 2 acts on fluid nodes with a solid neighbour; a solid node next to
+ * fluid takes the ghost value mean_d phi(s + 2d) - 2 h over the axis
+ * directions d with a fluid neighbour s + d (the flat-wall mirror; the
+ * diagonal directions if s touches fluid only through a corner).  Walls
+ * (params.walls) stay solid rows with h_bottom / h_top.  Solid nodes hold
+ * the rest state and report rho = phi = u = 0; they are left out of the
+ * statistics and of the interface points.  A domain with obstacles is
+ * stepped by two plain kernels per step instead of the staged one.
+ * The state must be initialised again afterwards (lb_init_*).
+ * Errors: LB_ERR_INVALID_ARG for a class out of range or without a
+ * gradient, a non-finite gradient, a map without fluid, or a solid node
+ * whose mirror node s + 2d is solid (features thinner than two nodes). */
+int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const double* h_class,
+                    int n_class);
+
+/* The obstacle map of domain dom (host [ny][nx]; all zero without one). */
+int lb_get_geometry(lb_handle* h, int dom, unsigned char* cls);
+
+/* Capillary filling set-up (Sec. VI) on a walled domain of nx x ny: the
+ * columns x >= res_len are solid except the channel rows [y0, y0 + ch_w),
+ * y0 = (ny - ch_w) / 2; the two solid rows bounding the channel are class 1
+ * (gradient h_channel), every other solid node class 2 (h_block).  The
+ * reservoir x < res_len connects to the channel outlet through the periodic
+ * x boundary.  Initial phi: phase alpha (+1) in the reservoir columns
+ * [res_len/2, res_len), beta (-1) elsewhere, flat tanh profiles
+ * (l = sqrt(2 kappa / a)) centred half a node before columns res_len/2 and
+ * res_len.  Then initialises as lb_init_phi.
+ * Errors: LB_ERR_INVALID_ARG without walls, for res_len outside
+ * [4, nx - 1], or a channel that leaves no solid row above or below it. */
+int lb_init_channel(lb_handle* h, int dom, int res_len, int ch_w, double h_channel,
+                    double h_block);
+
+/* Meniscus in a horizontal channel with walls at the planes y_lo - 1/2 and
+ * y_hi - 1/2 and phase alpha (phi > 0) behind it (smaller x), as in the
+ * capillary set-up: the phi = 0 points (as lb_contact_angle) on links with
+ * both ends in [x_lo, x_hi) x [y_lo, y_hi), farther than `exclude` from both
+ * wall planes, fitted with a circle.  x_front: the circle's x on the channel
+ * centre line, on the branch facing the points (l = x_front - (res_len -
+ * 1/2) is the filled length of Eq. washburnlaw); theta_deg: the angle
+ * through alpha at the walls (mean of both), the advancing angle theta^a of
+ * Sec. VI while the front moves; R: the radius.  Any output may be NULL.
+ * LB_ERR_NO_INTERFACE if fewer than 3 points remain. */
+int lb_meniscus(lb_handle* h, int dom, int x_lo, int x_hi, int y_lo, int y_hi, double exclude,
+                double* x_front, double* theta_deg, double* R);
+
 /* Wetting gradient h that Eq. (theory) assigns to an equilibrium angle
  * theta (degrees, 0..180): sqrt(2 kappa/a) h = 2 sgn(theta - 90)
  * [cos(alpha/3)(1 - cos(alpha/3))]^(1/2), alpha = arccos(sin^2 theta).

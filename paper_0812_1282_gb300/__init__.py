@@ -37,7 +37,8 @@ EXPORTS = (
     "lb_wetting_h", "lb_get_populations", "lb_get_populations_rows", "lb_set_populations", "lb_state_bytes",
     "lb_save_state", "lb_load_state", "lb_set_tile", "lb_get_tile", "lb_autotune",
     "lb_step_count", "lb_sync", "lb_launch_count", "lb_error_string", "lb_last_error",
-    "lb_stats_noalloc", "lb_check_wait_timeout",
+    "lb_stats_noalloc", "lb_check_wait_timeout", "lb_set_geometry", "lb_get_geometry",
+    "lb_init_channel", "lb_meniscus",
 )
 
 
@@ -133,6 +134,10 @@ def lib():
                 "lb_last_error": (ctypes.c_char_p, []),
                 "lb_stats_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
                 "lb_check_wait_timeout": (i, [vp]),
+                "lb_set_geometry": (i, [_H, i, vp, _D, i]),
+                "lb_get_geometry": (i, [_H, i, vp]),
+                "lb_init_channel": (i, [_H, i, i, i, d, d]),
+                "lb_meniscus": (i, [_H, i, i, i, i, i, d, _D, _D, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -247,6 +252,34 @@ class _HandleBase:
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
         assert phi0.shape == (self.nys[dom], self.nxs[dom])
         _check(lib().lb_init_phi(self.h, dom, _np_ptr(phi0), 0))
+
+    def set_geometry(self, cls, h_class, dom=0):
+        """Obstacle map (ny, nx) uint8 (0 fluid, k solid of class k) and the
+        classes' wetting gradients; None removes the obstacles."""
+        if cls is None:
+            _check(lib().lb_set_geometry(self.h, dom, None, None, 0))
+            return
+        cls = np.ascontiguousarray(cls, dtype=np.uint8)
+        assert cls.shape == (self.nys[dom], self.nxs[dom])
+        hc = np.ascontiguousarray(h_class, dtype=np.float64)
+        _check(lib().lb_set_geometry(self.h, dom, _np_ptr(cls), hc.ctypes.data_as(_D), len(hc)))
+
+    def geometry(self, dom=0):
+        cls = np.empty((self.nys[dom], self.nxs[dom]), dtype=np.uint8)
+        _check(lib().lb_get_geometry(self.h, dom, _np_ptr(cls)))
+        return cls
+
+    def init_channel(self, res_len, ch_w, h_channel, h_block=0.0, dom=0):
+        _check(lib().lb_init_channel(self.h, dom, int(res_len), int(ch_w), float(h_channel),
+                                     float(h_block)))
+
+    def meniscus(self, x_lo, x_hi, y_lo, y_hi, exclude=2.0, dom=0):
+        """(x_front, theta_deg, R) of a channel meniscus (see lb_meniscus)."""
+        xf, th, R = (ctypes.c_double() for _ in range(3))
+        _check(lib().lb_meniscus(self.h, dom, int(x_lo), int(x_hi), int(y_lo), int(y_hi),
+                                 float(exclude), ctypes.byref(xf), ctypes.byref(th),
+                                 ctypes.byref(R)))
+        return xf.value, th.value, R.value
 
     def step(self, n=1):
         _check(lib().lb_step(self.h, int(n)))

@@ -66,6 +66,8 @@ int pitch_for(int nx, int precision)
 struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
+    std::vector<size_t> geo_off;    // domain d's obstacle map (nx*ny bytes), then its phi field
+    std::vector<size_t> geo_phi;    // offset of domain d's phi field
     size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0,
            sched = 0;
     size_t total = 0;
@@ -89,6 +91,12 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
         L.dom_off.push_back(off);
         L.dom_bytes.push_back(buf);
         off += 2 * buf;
+        // room for an obstacle map and the per-node phi of the obstacle step
+        const size_t nodes = size_t(nx[d]) * size_t(ny[d]);
+        L.geo_off.push_back(off);
+        off = align_up(off + nodes, kAlign);
+        L.geo_phi.push_back(off);
+        off = align_up(off + nodes * es, kAlign);
         max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
         max_nx = std::max<long long>(max_nx, nx[d]);
         item_cap += (long long)((nx[d] + kMinBlockX - 1) / kMinBlockX) * ny[d];
@@ -172,6 +180,7 @@ struct lb_handle {
     long long launches = 0;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (length, start parity)
     std::vector<double> host_pts;
+    int n_geo = 0;  // domains with an obstacle map
 
     DomDesc* d_descs() const { return reinterpret_cast<DomDesc*>(base + L.descs); }
     WorkItem* d_items() const { return reinterpret_cast<WorkItem*>(base + L.items); }
@@ -210,6 +219,7 @@ int build_items(lb_handle* h)
     std::vector<WorkItem> items;
     for (int d : order) {
         const DomDesc& D = h->descs[d];
+        if (D.cls) continue;  // stepped by the obstacle kernels
         for (int y0 = 0; y0 < D.ny; y0 += h->rows)
             for (int x0 = 0; x0 < D.nx; x0 += h->block_x)
                 items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0)});
@@ -217,21 +227,43 @@ int build_items(lb_handle* h)
     if ((long long)items.size() > h->L.item_cap)
         return fail(LB_ERR_INVALID_ARG, "work list exceeds its capacity");
     h->n_items = int(items.size());
-    LB_CUDA(cudaMemcpyAsync(h->d_items(), items.data(), sizeof(WorkItem) * items.size(),
-                            cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        LB_CUDA(cudaMemcpyAsync(h->d_items(), items.data(), sizeof(WorkItem) * items.size(),
+                                cudaMemcpyHostToDevice, h->stream));
     LB_CUDA(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 
+// One time step of every domain: the staged kernel for the domains without
+// obstacles (one launch: the single-domain grid, or the persistent kernel
+// over the batch's work list), then two launches per domain with obstacles.
 int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
 {
-    const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
-                                    h->n_dom > 1 ? h->d_items() : nullptr, h->n_items, h->n_dom,
-                                    parity, h->block_x, h->rows, h->grid_persistent, h->d_sched(),
-                                    s);
-    if (e != 0)
-        return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
+    if (plain) {
+        const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
+                                        h->n_dom > 1 ? h->d_items() : nullptr, h->n_items,
+                                        h->n_dom, parity, h->block_x, h->rows,
+                                        h->grid_persistent, h->d_sched(), s);
+        if (e != 0)
+            return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    }
+    if (h->n_geo > 0)
+        for (const DomDesc& D : h->descs) {
+            if (!D.cls) continue;
+            const int e = lbfe::launch_geo_step(h->precision, h->coll, D, parity, s);
+            if (e != 0)
+                return fail(LB_ERR_CUDA, "obstacle step launch failed: %s",
+                            cudaGetErrorString(cudaError_t(e)));
+        }
     return LB_OK;
+}
+
+// Kernel launches of one time step.
+long long launches_per_step(const lb_handle* h)
+{
+    const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
+    return (plain ? 1 : 0) + 2LL * h->n_geo;
 }
 
 int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
@@ -304,10 +336,18 @@ int finish_init(lb_handle* h, int dom)
 {
     // every domain of a handle shares one parity; the new state goes to the
     // current buffer, phi0 sat in the other one
-    const int e = lbfe::launch_init_eq(h->precision, h->descs[dom], phi0_scratch(h, dom),
-                                       h->parity, h->stream);
+    const DomDesc& D = h->descs[dom];
+    int e;
+    if (D.cls) {
+        e = lbfe::launch_geo_init_eq(h->precision, D, phi0_scratch(h, dom), h->parity, h->stream);
+        // solid nodes of the idle buffer (phi0 is consumed by now): rest state
+        if (e == 0) e = lbfe::launch_geo_solid_rest(h->precision, D, h->parity ^ 1, h->stream);
+        h->launches += 2;
+    } else {
+        e = lbfe::launch_init_eq(h->precision, D, phi0_scratch(h, dom), h->parity, h->stream);
+        h->launches += 1;
+    }
     if (e != 0) return fail(LB_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(cudaError_t(e)));
-    h->launches += 1;
     h->steps = 0;
     return LB_OK;
 }
@@ -411,6 +451,12 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.ftau_c1 = float(D.tau_c1);
         D.fh_bot = float(D.h_bot);
         D.fh_top = float(D.h_top);
+        D.cls = nullptr;
+        D.phi = h->base + L.geo_phi[d];
+        for (int k = 0; k < 8; ++k) {
+            D.hcls[k] = 0.0;
+            D.fhcls[k] = 0.0f;
+        }
         h->descs.push_back(D);
     }
     if ((e = cudaMemsetAsync(h->base, 0, L.total, h->stream)) != cudaSuccess ||
@@ -497,6 +543,48 @@ bool fit_circle(const std::vector<double>& pts, double& xc, double& yc, double& 
     yc = cy + my;
     R = rr;
     return std::isfinite(xc) && std::isfinite(yc) && std::isfinite(R) && R > 0;
+}
+
+// Host check of an obstacle map (the rules of the obstacle step): classes
+// in range, some fluid, and every solid node next to fluid (wall rows
+// included) has fluid mirror nodes s + 2d in the directions its ghost value
+// uses.
+int check_geometry(const unsigned char* cls, int nx, int ny, int walls)
+{
+    auto solid = [&](int x, int y) {
+        if (walls && (y < 0 || y >= ny)) return true;
+        x = ((x % nx) + nx) % nx;
+        y = ((y % ny) + ny) % ny;
+        return cls[size_t(y) * nx + x] != 0;
+    };
+    long long fluid = 0;
+    for (size_t k = 0; k < size_t(nx) * ny; ++k) {
+        if (cls[k] > lbfe::kMaxClass)
+            return fail(LB_ERR_INVALID_ARG, "class %d at node %zu exceeds %d", int(cls[k]), k,
+                        lbfe::kMaxClass);
+        fluid += cls[k] == 0;
+    }
+    if (fluid == 0) return fail(LB_ERR_INVALID_ARG, "the obstacle map has no fluid node");
+    static const int AX[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    static const int DG[4][2] = {{1, 1}, {-1, -1}, {-1, 1}, {1, -1}};
+    for (int y = walls ? -1 : 0; y < (walls ? ny + 1 : ny); ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!solid(x, y)) continue;
+            int n = 0;
+            for (auto& d : AX)
+                if (!solid(x + d[0], y + d[1])) {
+                    ++n;
+                    if (solid(x + 2 * d[0], y + 2 * d[1]))
+                        return fail(LB_ERR_INVALID_ARG,
+                                    "solid node (%d, %d): feature thinner than two nodes", x, y);
+                }
+            if (n > 0) continue;
+            for (auto& d : DG)
+                if (!solid(x + d[0], y + d[1]) && solid(x + 2 * d[0], y + 2 * d[1]))
+                    return fail(LB_ERR_INVALID_ARG,
+                                "solid node (%d, %d): feature thinner than two nodes", x, y);
+        }
+    return LB_OK;
 }
 
 }  // namespace
@@ -593,7 +681,7 @@ int lb_step(lb_handle* h, int n)
         }
         if (len & 1) h->parity ^= 1;
         h->steps += len;
-        h->launches += len;
+        h->launches += len * launches_per_step(h);
         n -= len;
     }
     return LB_OK;
@@ -698,6 +786,157 @@ int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg, d
     if (R) *R = rr;
     if (xc) *xc = cx;
     if (yc) *yc = cy;
+    return LB_OK;
+}
+
+int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const double* h_class,
+                    int n_class)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    DomDesc& D = h->descs[dom];
+    if (cls) {
+        if (!h_class || n_class < 1 || n_class > lbfe::kMaxClass + 1)
+            return fail(LB_ERR_INVALID_ARG, "h_class must hold 1..%d entries", lbfe::kMaxClass + 1);
+        for (int k = 0; k < n_class; ++k)
+            if (!std::isfinite(h_class[k]))
+                return fail(LB_ERR_INVALID_ARG, "wetting gradient of class %d is not finite", k);
+        for (size_t q = 0; q < size_t(D.nx) * D.ny; ++q)
+            if (cls[q] >= n_class)
+                return fail(LB_ERR_INVALID_ARG, "node %zu has class %d but only %d classes given",
+                            q, int(cls[q]), n_class);
+        rc = check_geometry(cls, D.nx, D.ny, D.walls);
+        if (rc != LB_OK) return rc;
+    }
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    unsigned char* dev = h->base + h->L.geo_off[dom];
+    const bool had = D.cls != nullptr;
+    if (cls) {
+        LB_CUDA(cudaMemcpyAsync(dev, cls, size_t(D.nx) * D.ny, cudaMemcpyHostToDevice, h->stream));
+        D.cls = dev;
+        for (int k = 0; k < 8; ++k) {
+            D.hcls[k] = k < n_class ? h_class[k] : 0.0;
+            D.fhcls[k] = float(D.hcls[k]);
+        }
+    } else {
+        D.cls = nullptr;
+    }
+    h->n_geo += (D.cls != nullptr) - int(had);
+    LB_CUDA(cudaMemcpyAsync(h->d_descs() + dom, &D, sizeof(DomDesc), cudaMemcpyHostToDevice,
+                            h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return build_items(h);
+}
+
+int lb_get_geometry(lb_handle* h, int dom, unsigned char* cls)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!cls) return fail(LB_ERR_INVALID_ARG, "cls is NULL");
+    const DomDesc& D = h->descs[dom];
+    if (!D.cls) {
+        memset(cls, 0, size_t(D.nx) * D.ny);
+        return LB_OK;
+    }
+    LB_CUDA(cudaMemcpyAsync(cls, D.cls, size_t(D.nx) * D.ny, cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_init_channel(lb_handle* h, int dom, int res_len, int ch_w, double h_channel,
+                    double h_block)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    const DomDesc& D0 = h->descs[dom];
+    const int nx = D0.nx, ny = D0.ny;
+    if (!D0.walls) return fail(LB_ERR_INVALID_ARG, "the capillary set-up needs walls");
+    if (res_len < 4 || nx - res_len < 1)
+        return fail(LB_ERR_INVALID_ARG, "res_len must be in [4, nx - 1]");
+    const int y0 = (ny - ch_w) / 2;
+    if (ch_w < 2 || y0 < 1 || y0 + ch_w + 1 > ny)
+        return fail(LB_ERR_INVALID_ARG, "channel width must leave a solid row on each side");
+    if (!std::isfinite(h_channel) || !std::isfinite(h_block))
+        return fail(LB_ERR_INVALID_ARG, "wetting gradients must be finite");
+    std::vector<unsigned char> cls(size_t(nx) * ny, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = res_len; x < nx; ++x) {
+            unsigned char c = 2;
+            if (y >= y0 && y < y0 + ch_w) c = 0;
+            if (y == y0 - 1 || y == y0 + ch_w) c = 1;
+            cls[size_t(y) * nx + x] = c;
+        }
+    const double hc[3] = {0.0, h_channel, h_block};
+    rc = lb_set_geometry(h, dom, cls.data(), hc, 3);
+    if (rc != LB_OK) return rc;
+    // phase alpha in the reservoir columns [res_len/2, res_len), beta elsewhere;
+    // flat tanh profiles centred half a node before each interface column
+    const DomDesc& D = h->descs[dom];
+    const double l = std::sqrt(2.0 * D.kappa / D.a);
+    const double xa = res_len / 2 - 0.5, xb = res_len - 0.5;
+    std::vector<double> phi0(size_t(nx) * ny);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t k = size_t(y) * nx + x;
+            phi0[k] = cls[k] ? 0.0 : std::tanh(std::min(x - xa, xb - x) / l);
+        }
+    return lb_init_phi(h, dom, phi0.data(), 0);
+}
+
+int lb_meniscus(lb_handle* h, int dom, int x_lo, int x_hi, int y_lo, int y_hi, double exclude,
+                double* x_front, double* theta_deg, double* R)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    const DomDesc& D = h->descs[dom];
+    if (x_lo < 0 || x_hi > D.nx || x_lo + 2 > x_hi || y_lo < 0 || y_hi > D.ny || y_lo + 2 > y_hi ||
+        !std::isfinite(exclude))
+        return fail(LB_ERR_INVALID_ARG, "bad meniscus box");
+    const int cap = 16 * (D.nx + D.ny);
+    const int e = lbfe::launch_crossings(h->precision, D, h->parity, h->d_pts(), h->d_count(), cap,
+                                         h->stream);
+    if (e != 0) return fail(LB_ERR_CUDA, "crossings launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    h->launches += 1;
+    int count = 0;
+    LB_CUDA(cudaMemcpyAsync(&count, h->d_count(), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    if (count > cap) return fail(LB_ERR_CAPACITY, "%d interface points exceed capacity %d", count, cap);
+    std::vector<double> raw(2 * size_t(count));
+    if (count > 0) {
+        LB_CUDA(cudaMemcpyAsync(raw.data(), h->d_pts(), sizeof(double) * 2 * count,
+                                cudaMemcpyDeviceToHost, h->stream));
+        LB_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    // points on links with both ends in the box, away from the walls
+    const double wb = y_lo - 0.5, wt = y_hi - 0.5;
+    std::vector<std::pair<double, double>> pts;
+    for (int i = 0; i < count; ++i) {
+        const double px = raw[2 * i], py = raw[2 * i + 1];
+        if (px < x_lo || px > x_hi - 1 || py < y_lo || py > y_hi - 1) continue;
+        if (py < wb + exclude || py > wt - exclude) continue;
+        pts.emplace_back(px, py);
+    }
+    std::sort(pts.begin(), pts.end());
+    if (pts.size() < 3) return fail(LB_ERR_NO_INTERFACE, "only %zu meniscus points", pts.size());
+    std::vector<double> flat;
+    double mx = 0.0;
+    for (auto& q : pts) {
+        flat.push_back(q.first);
+        flat.push_back(q.second);
+        mx += q.first;
+    }
+    mx /= double(pts.size());
+    double cx, cy, rr;
+    if (!fit_circle(flat, cx, cy, rr)) return fail(LB_ERR_NO_INTERFACE, "circle fit failed");
+    // centre ahead of the points (beta side): alpha wets the walls
+    const double sg = cx > mx ? 1.0 : -1.0;
+    auto clampc = [](double v) { return std::max(-1.0, std::min(1.0, v)); };
+    const double tb = std::acos(clampc(sg * (cy - wb) / rr)), tt = std::acos(clampc(sg * (wt - cy) / rr));
+    const double ym = 0.5 * (wb + wt);
+    if (x_front) *x_front = cx - sg * std::sqrt(std::max(rr * rr - (ym - cy) * (ym - cy), 0.0));
+    if (theta_deg) *theta_deg = 0.5 * (tb + tt) * 180.0 / M_PI;
+    if (R) *R = rr;
     return LB_OK;
 }
 
@@ -869,8 +1108,15 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     if (reps < 1) reps = 1;
     int max_ny = 0;
     for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
-    const int bxs[] = {64, 128, 256};
-    const int rws[] = {4, 8, 16, 32, 64, 128};
+    // with obstacles only, no domain uses the staged kernel: nothing to tune
+    const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
+    const int bxs_all[] = {64, 128, 256};
+    const int rws_all[] = {4, 8, 16, 32, 64, 128};
+    std::vector<int> bxs(bxs_all, bxs_all + 3), rws(rws_all, rws_all + 6);
+    if (!plain) {
+        bxs.assign(1, h->block_x);
+        rws.assign(1, h->rows);
+    }
     cudaEvent_t e0, e1;
     LB_CUDA(cudaEventCreate(&e0));
     LB_CUDA(cudaEventCreate(&e1));
@@ -880,7 +1126,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     int rc = LB_OK;
     for (int bx : bxs) {
         for (int r : rws) {
-            if (r > max_ny && r != rws[0]) continue;
+            if (r > max_ny && r != rws.front()) continue;
             if ((rc = lb_set_tile(h, bx, r)) != LB_OK) break;
             // warm-up, then time `reps` launches that read the current buffer
             // and write the idle one (the state itself does not advance)
@@ -895,7 +1141,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
             }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            h->launches += reps + 1;
+            h->launches += (reps + 1) * launches_per_step(h);
             if (ms / reps < best) {
                 best = ms / reps;
                 bb = bx;

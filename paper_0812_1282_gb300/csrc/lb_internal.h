@@ -31,7 +31,17 @@ struct DomDesc {
     // the same parameters rounded to float once on the host (the FP32 step
     // reads these; converting in the kernel would run on the slow FP64 pipe)
     float fa, fkappa, fgamma, fomega_phi, ftau_c0, ftau_c1, fh_bot, fh_top;
+    // Obstacles (nullptr: none).  cls[y * nx + x] = 0 for a fluid node, k in
+    // 1..kMaxClass for a solid node of wetting class k with inward-normal
+    // wetting gradient hcls[k].  phi: per-node order parameter written by the
+    // first of the two kernels of an obstacle step ([ny][nx], Real).
+    const unsigned char* cls;
+    void* phi;
+    double hcls[8];
+    float fhcls[8];
 };
+
+constexpr int kMaxClass = 7;
 
 // A rectangular piece of one domain processed by one CTA: columns
 // [x0, x0 + blockDim.x) and rows [y0, y0 + rows).
@@ -66,6 +76,13 @@ int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nr
 int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, int* count,
                      int cap, void* stream);
 int launch_fill_ghosts(int precision, const DomDesc& d, int parity, void* stream);
+
+// Domains with obstacles (d.cls != nullptr): one time step (two kernels),
+// the initial equilibrium, and the rest state of the solid nodes of buffer b.
+int launch_geo_step(int precision, int coll, const DomDesc& d, int parity, void* stream);
+int launch_geo_init_eq(int precision, const DomDesc& d, const double* phi0, int parity,
+                       void* stream);
+int launch_geo_solid_rest(int precision, const DomDesc& d, int b, void* stream);
 
 // Opt the step kernels in to large dynamic shared memory (call once per
 // device before the first launch, outside any stream capture).

@@ -366,6 +366,15 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int yr = int(k / nx), x = int(k - (long long)yr * nx);
+        const long long q = (long long)yr * ld + x;
+        if (D.cls && D.cls[(long long)(row0 + yr) * nx + x] != 0) {
+            // solid node: no fluid, no contribution to the diagnostics
+            if (rho) rho[q] = 0.0;
+            if (phi) phi[q] = 0.0;
+            if (ux) ux[q] = 0.0;
+            if (uy) uy[q] = 0.0;
+            continue;
+        }
         const long long o = (long long)(row0 + yr) * pitch + x + kXOff;
         double f[9], g[9];
         for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
@@ -377,7 +386,6 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
         const double ph = phi_sum<double>(g);
         const double r = 1.0 + drho;
         const double vx = jx / r, vy = jy / r;
-        const long long q = (long long)yr * ld + x;
         if (rho) rho[q] = r;
         if (phi) phi[q] = ph;
         if (ux) ux[q] = vx;
@@ -465,8 +473,9 @@ int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nr
 
 // ----------------------------------------------------- interface points
 // phi = 0 crossings on horizontal (periodic) and vertical links whose ends
-// have phi > 0 and phi < 0, by linear interpolation (Sec. IV).  Points are
-// appended in arbitrary order; the host sorts them.
+// have phi > 0 and phi < 0, by linear interpolation (Sec. IV); links that
+// touch a solid node are skipped.  Points are appended in arbitrary order;
+// the host sorts them.
 template <typename Real>
 __device__ __forceinline__ double phi_at_node(const Real* g, long long P, long long o)
 {
@@ -486,17 +495,20 @@ __global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count,
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int y = int(k / nx), x = int(k - (long long)y * nx);
+        const unsigned char* cls = D.cls;
+        if (cls && cls[k] != 0) continue;  // links touching a solid node carry no interface
         const double a = phi_at_node(gs, P, (long long)y * pitch + x + kXOff);
         const int xp = x + 1 == nx ? 0 : x + 1;
         const double b = phi_at_node(gs, P, (long long)y * pitch + xp + kXOff);
-        if ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0)) {
+        const bool bfluid = !cls || cls[(long long)y * nx + xp] == 0;
+        if (bfluid && ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0))) {
             const int idx = atomicAdd(count, 1);
             if (idx < cap) {
                 pts[2 * idx] = x + a / (a - b);
                 pts[2 * idx + 1] = double(y);
             }
         }
-        if (y + 1 < ny) {
+        if (y + 1 < ny && (!cls || cls[(long long)(y + 1) * nx + x] == 0)) {
             const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x + kXOff);
             if ((a > 0.0 && c < 0.0) || (a < 0.0 && c > 0.0)) {
                 const int idx = atomicAdd(count, 1);
