@@ -23,6 +23,7 @@ on the data path); rank 0 prints.
 from __future__ import annotations
 
 import argparse
+import math
 import ctypes
 import glob
 import hashlib
@@ -256,6 +257,59 @@ def run_fp64(lbf, torch, steps):
                 gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9)
 
 
+def run_capillary(lbf, torch, steps=None):
+    """Capillary filling (Sec. VI) on the 1000 x 120 set-up in FP32: the
+    whole job (obstacle step, the meniscus fitted every 500 steps) timed on
+    the host clock, and the Washburn force-balance fit of the filled length
+    over the second half."""
+    import numpy as np
+
+    c = lbinputs.CAPILLARY_1000x120
+    steps = steps or c["steps"]
+    p = lbf.params(precision="fp32", **c["params"])
+    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim.init_channel(c["res_len"], c["ch_w"], lbf.lb_wetting_h(c["theta"]), c["h_block"])
+    fluid = int((sim.geometry() == 0).sum())
+    y0 = (c["ny"] - c["ch_w"]) // 2
+    ts, ls, ths = [], [], []
+    sim.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = 2
+    while done < steps:
+        k = min(c["every"] - done % c["every"], steps - done)
+        sim.step(k)
+        done += k
+        xf, th, _ = sim.meniscus(c["res_len"], c["nx"], y0, y0 + c["ch_w"])
+        ts.append(done)
+        ls.append(xf - (c["res_len"] - 0.5))
+        ths.append(th)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dt_steps = time_steps(sim, 2000, torch)
+    st = sim.stats()
+    sim.close()
+    t = np.array(ts, float)
+    l = np.array(ls)
+    nua = (c["params"]["tau_alpha"] - 0.5) / 3
+    nub = (c["params"]["tau_beta"] - 0.5) / 3
+    L = c["nx"] - c["res_len"]
+    Y = (nua - nub) * l * l / 2 + nub * L * l
+    late = t >= t[-1] / 2
+    slope = float(np.polyfit(t[late], Y[late], 1)[0])
+    theta_a = float(np.mean(np.array(ths)[late]))
+    gamma = math.sqrt(8 * c["params"]["a"] * c["params"]["kappa"] / 9)
+    k_theory = gamma * c["ch_w"] * math.cos(math.radians(theta_a)) / 6.0
+    return dict(steps=steps, fluid_nodes=fluid, job_seconds=wall,
+                step_us=dt_steps / 2000 * 1e6, mlups_fluid=fluid * 2000 / dt_steps / 1e6,
+                l_final=float(l[-1]), theta_a_late=theta_a,
+                washburn_slope=slope, washburn_slope_theory=k_theory,
+                nonfinite=int(st["nonfinite"]),
+                note="obstacle path, two launches per step; front by lb_meniscus every 500 "
+                     "steps; Washburn fit (nu_a - nu_b) l^2/2 + nu_b L l vs t over the second "
+                     "half, theory gamma w cos(theta_a) / 6")
+
+
 def run_batched(lbf, torch, steps):
     """256 sessile drops (sides 64..512) in one launch per step, against the
     same domains stepped one after another (one launch per domain per step)."""
@@ -412,6 +466,11 @@ def ours(args):
             extras["batched"] = run_batched(lbf, torch, max(20, args.steps // 2))
         except Exception as exc:
             extras["batched"] = {"error": str(exc)}
+        torch.cuda.empty_cache()
+        try:
+            extras["capillary"] = run_capillary(lbf, torch)
+        except Exception as exc:
+            extras["capillary"] = {"error": str(exc)}
         line["extras"] = extras
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -457,6 +516,54 @@ def reference(args):
     }), flush=True)
 
 
+def experiment_ramp():
+    """The paper's quasi-static ramp (Sec. IV): 300 x 100, drop R = 35 at
+    90 degrees, a = kappa = 0.04, Gamma = 0.5, tau_alpha 3 / tau_beta 0.7;
+    3e4 steps at h = 0, then h changed linearly over 1e6 steps towards
+    h(160 deg) (up) or h(20 deg) (down), every 1000 steps, the angle read
+    every 20000 steps; BGK, MRT and MRT with the relaxed Step-2 momentum.
+    FP32 on the GPU; prints one JSON object per branch."""
+    import paper_0812_1282_gb300 as lbf
+
+    def theta_theory(h):
+        # Eq. (theory) inverted by bisection on the library's monotone h(theta)
+        lo, hi = 0.0, 180.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if lbf.lb_wetting_h(mid) < h:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    for coll, relax in (("mrt", False), ("mrt", True), ("bgk", False)):
+        for direction, theta_end in (("up", 160.0), ("down", 20.0)):
+            p = lbf.params(a=0.04, kappa=0.04, gamma_mob=0.5, tau_alpha=3.0, tau_beta=0.7,
+                           collision=coll, precision="fp32", step2_relax_momentum=relax)
+            sim = lbf.Lattice(p, 300, 100)
+            sim.init_drop(35.0, 150.0, -0.5)
+            sim.step(30000)
+            h_end = lbf.lb_wetting_h(theta_end)
+            rows, t, n = [], 0, 1000000
+            while t < n:
+                sim.step(1000)
+                t += 1000
+                h = h_end * t / n
+                sim.set_wetting(h, 0.0)
+                if t % 20000 == 0:
+                    if sim.stats()["nonfinite"]:
+                        rows.append([t, h, None])
+                        break
+                    rows.append([t, h, round(sim.contact_angle()[0], 3)])
+            sim.close()
+            print(json.dumps({"collision": coll, "step2_relax_momentum": relax,
+                              "branch": direction,
+                              "rows": [[r[0], round(r[1], 5), round(theta_theory(r[1]), 3),
+                                        r[2]] for r in rows],
+                              "columns": ["step", "h", "theta_theory", "theta_measured"]}),
+                  flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,10 +575,15 @@ def main():
                     help="side of a smaller square lattice (profiling aid; default 8192)")
     ap.add_argument("--tile", default=None,
                     help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
+    ap.add_argument("--experiment", choices=("ramp",), default=None,
+                    help="run a physics experiment instead of the benchmark and print its "
+                         "JSON table (ramp: the quasi-static wetting ramp of Sec. IV)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.experiment == "ramp":
+        experiment_ramp()
+    elif args.impl == "reference":
         reference(args)
     else:
         ours(args)

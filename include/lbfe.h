@@ -72,6 +72,10 @@ typedef struct lb_params {
     int step2_relax_momentum; /* MRT only: on Step-2 rows the momentum rows of Eq. (diag)
                                  relax at rate 1 (wall-row momentum set to zero) instead of
                                  the literal rate 0 of the conserved moments (default 0) */
+    int mrt_lut;         /* MRT only: 0 (default) uses the exact tau(phi) of Eq. (tau) at
+                            every node; n >= 2 uses the nearest of n viscosities spaced
+                            evenly between tau_beta and tau_alpha (ends included, the end
+                            values beyond them): the lookup table of Sec. V            */
 } lb_params;
 
 /* Diagnostics of one domain (sums over all nodes, in FP64). */
@@ -180,6 +184,13 @@ int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
  * whose mirror node s + 2d is solid (features thinner than two nodes). */
 int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const double* h_class,
                     int n_class);
+
+/* Change the wall wetting gradients of domain dom between steps, keeping the
+ * state (the quasi-static ramp of the wetting gradient in Sec. IV, by which
+ * the paper moves a drop through a sequence of equilibrium angles).  Takes
+ * effect from the next step; synchronises the stream.
+ * Errors: LB_ERR_INVALID_ARG for non-finite gradients. */
+int lb_set_wetting(lb_handle* h, int dom, double h_bottom, double h_top);
 
 /* The obstacle map of domain dom (host [ny][nx]; all zero without one). */
 int lb_get_geometry(lb_handle* h, int dom, unsigned char* cls);

@@ -15,6 +15,11 @@ stated; x periodic; bounce-back walls at y = 0 and y = ny - 1):
                    rates), drop R = 40; viscosity ratio 1 (tau 1 / 1) and
                    10 (tau_alpha 1.5 drop, tau_beta 0.6 gas); target
                    angles 60, 90, 120 degrees; 20000 steps.
+  CAPILLARY_1000x120  capillary filling: walled 1000 x 120 box, reservoir
+                   columns 0..199 (alpha in 100..199), channel rows 40..79
+                   from column 200 on, h(60 deg) on the channel walls,
+                   neutral elsewhere; MRT, tau_alpha 1.5, tau_beta 0.6;
+                   100000 steps, front tracked every 500.
   SPINODAL_8192    MRT, tau_alpha 1.5, tau_beta 0.6, neutral walls,
                    phi uniform in [-0.1, 0.1) from SplitMix64 seed 12345
                    (node (x, y) takes draw y*nx + x); FP32 and FP64.
@@ -83,6 +88,11 @@ SWEEP_200x100 = dict(nx=200, ny=100, R=40.0, cx=100.0, cy=-0.5, steps=20000,
                      # (collision, step2_relax_momentum)
                      variants=(("bgk", False), ("mrt", False), ("mrt", True)),
                      check_every=500)
+
+CAPILLARY_1000x120 = dict(nx=1000, ny=120, res_len=200, ch_w=40, theta=60.0, h_block=0.0,
+                          steps=100000, every=500,
+                          params=dict(BASE, collision="mrt", tau_alpha=1.5, tau_beta=0.6,
+                                      h_bottom=0.0, h_top=0.0))
 
 SPINODAL_8192 = dict(nx=8192, ny=8192, amp=0.1, seed=12345, steps=1000,
                      sub=512,

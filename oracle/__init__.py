@@ -62,14 +62,14 @@ class OrcParams(ctypes.Structure):
         ("h_bottom", ctypes.c_double), ("h_top", ctypes.c_double),
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("walls", ctypes.c_int), ("mrt_all_rates", ctypes.c_int),
-        ("step2_relax_momentum", ctypes.c_int),
+        ("step2_relax_momentum", ctypes.c_int), ("mrt_lut", ctypes.c_int),
     ]
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
            tau_beta=1.0, h_bottom=0.0, h_top=0.0, collision="bgk",
            zero_u_at_walls=None, walls=True, mrt_all_rates=False,
-           step2_relax_momentum=False) -> OrcParams:
+           step2_relax_momentum=False, mrt_lut=0) -> OrcParams:
     """Parameter block.  ``zero_u_at_walls`` defaults to on for MRT (the
     proposed algorithm of Sec. V) and off for BGK."""
     coll = {"bgk": 0, "mrt": 1}[collision] if isinstance(collision, str) else int(collision)
@@ -77,7 +77,7 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
         zero_u_at_walls = coll == 1
     return OrcParams(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom,
                      h_top, coll, int(bool(zero_u_at_walls)), int(bool(walls)),
-                     int(bool(mrt_all_rates)), int(bool(step2_relax_momentum)))
+                     int(bool(mrt_all_rates)), int(bool(step2_relax_momentum)), int(mrt_lut))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -117,6 +117,7 @@ def lib():
                 "orc_moments": (None, [i, i, _D, _D, _D, _D, _D, _D]),
                 "orc_step_window": (i, [P, i, i, i, i, _D, _D, i, i, i, i, _D, _D]),
                 "orc_geo_check": (i, [P, i, i, _U8]),
+                "orc_node_tau": (d, [P, d]),
                 "orc_phi_derivatives_geo": (None, [P, i, i, _U8, _D, _D, _D, _D, _D]),
                 "orc_init_geo": (i, [P, i, i, _U8, _D, _D, _D, _D]),
                 "orc_step_geo": (i, [P, i, i, _U8, _D, _D, _D, i]),
@@ -162,6 +163,12 @@ def node_collide_f(p: OrcParams, f, feq, omega, step2_node=False):
     lib().orc_node_collide_f(ctypes.byref(p), _ptr(f), _ptr(feq), float(omega),
                              int(bool(step2_node)), _ptr(out))
     return out
+
+
+def node_tau(p: OrcParams, phi: float) -> float:
+    """tau_rho the step uses at a node of order parameter phi (Eq. tau, or
+    the nearest tabulated value with the lookup table of Sec. V)."""
+    return float(lib().orc_node_tau(ctypes.byref(p), float(phi)))
 
 
 def phi_derivatives(p: OrcParams, phi: np.ndarray):

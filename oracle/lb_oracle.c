@@ -60,6 +60,8 @@ typedef struct orc_params {
     int mrt_all_rates;        /* test mode: every S entry equal to omega    */
     int step2_relax_momentum; /* MRT: momentum rows relax at rate 1 on Step-2
                                  nodes (default 0: the literal zeros of Eq. diag) */
+    int mrt_lut;              /* MRT: 0 = exact tau(phi); n >= 2 = the nearest of n
+                                 tabulated viscosities (Sec. V lookup table)  */
 } orc_params;
 
 /* ---------------------------------------------------------------- lattice */
@@ -132,6 +134,22 @@ void orc_mrt_matrix(double* m_out, double* minv_out)
 }
 
 static inline int wrap(int v, int n) { return ((v % n) + n) % n; }
+
+/* tau_rho at a node of order parameter phi: Eq. tau, or with the lookup
+ * table of Sec. V (MRT only) the nearest of mrt_lut values spaced evenly
+ * between the two bulk values (ends included; beyond them the end value). */
+double orc_node_tau(const orc_params* p, double phi)
+{
+    const double tau = p->tau_beta + 0.5 * (phi + 1.0) * (p->tau_alpha - p->tau_beta);
+    if (p->collision != 1 || p->mrt_lut < 2 || p->tau_alpha == p->tau_beta) return tau;
+    const double lo = p->tau_alpha < p->tau_beta ? p->tau_alpha : p->tau_beta;
+    const double hi = p->tau_alpha < p->tau_beta ? p->tau_beta : p->tau_alpha;
+    const double step = (hi - lo) / (p->mrt_lut - 1);
+    double k = nearbyint((tau - lo) / step);
+    if (k < 0.0) k = 0.0;
+    if (k > p->mrt_lut - 1) k = p->mrt_lut - 1;
+    return lo + k * step;
+}
 
 /* --------------------------------------------------------- equilibria */
 /* Eq. equilibrium and Eq. feq0 at one node.  u is the velocity used in the
@@ -393,8 +411,7 @@ void orc_step(const orc_params* p, int nx, int ny, double* f, double* g, int nst
                 orc_node_equilibrium(p, rho[kk], phi[kk], ueqx, ueqy, dx[kk], dy[kk],
                                      lap[kk], feq, geq);
                 /* Eq. tau */
-                const double tau = p->tau_beta +
-                                   0.5 * (phi[kk] + 1.0) * (p->tau_alpha - p->tau_beta);
+                const double tau = orc_node_tau(p, phi[kk]); /* Eq. tau */
                 const double omega = 1.0 / tau;
                 for (int i = 0; i < 9; ++i) fin[i] = fs[(size_t)i * n + kk];
                 collide_f(p, minv, fin, feq, omega, step2_node, fout);
@@ -538,7 +555,7 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
             }
             double feq[9], geq[9], fo[9];
             orc_node_equilibrium(p, r, ph, ueqx, ueqy, dxv, dyv, lapv, feq, geq);
-            const double tau = p->tau_beta + 0.5 * (ph + 1.0) * (p->tau_alpha - p->tau_beta);
+            const double tau = orc_node_tau(p, ph);
             collide_f(p, minv, fin, feq, 1.0 / tau, step2_node, fo);
             const size_t wk = (size_t)(y - y0) * wx + (x - x0);
             for (int i = 0; i < 9; ++i) {
@@ -794,8 +811,7 @@ int orc_step_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
                 double feq[9], geq[9], fin[9], fout[9];
                 orc_node_equilibrium(p, rho[kk], phi[kk], ueqx, ueqy, dx[kk], dy[kk], lap[kk],
                                      feq, geq);
-                const double tau = p->tau_beta +
-                                   0.5 * (phi[kk] + 1.0) * (p->tau_alpha - p->tau_beta);
+                const double tau = orc_node_tau(p, phi[kk]);
                 for (int i = 0; i < 9; ++i) fin[i] = fs[(size_t)i * n + kk];
                 collide_f(p, minv, fin, feq, 1.0 / tau, step2_node, fout);
                 for (int i = 0; i < 9; ++i) {

@@ -38,7 +38,7 @@ EXPORTS = (
     "lb_save_state", "lb_load_state", "lb_set_tile", "lb_get_tile", "lb_autotune",
     "lb_step_count", "lb_sync", "lb_launch_count", "lb_error_string", "lb_last_error",
     "lb_stats_noalloc", "lb_check_wait_timeout", "lb_set_geometry", "lb_get_geometry",
-    "lb_init_channel", "lb_meniscus",
+    "lb_init_channel", "lb_meniscus", "lb_set_wetting",
 )
 
 
@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
         ("h_bottom", ctypes.c_double), ("h_top", ctypes.c_double),
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("precision", ctypes.c_int), ("walls", ctypes.c_int),
-        ("step2_relax_momentum", ctypes.c_int),
+        ("step2_relax_momentum", ctypes.c_int), ("mrt_lut", ctypes.c_int),
     ]
 
 
@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,
            h_bottom=0.0, h_top=0.0, collision="bgk", zero_u_at_walls=None,
-           precision="fp64", walls=True, step2_relax_momentum=False) -> Params:
+           precision="fp64", walls=True, step2_relax_momentum=False, mrt_lut=0) -> Params:
     """Parameter block (lattice units).  Step 2 of the proposed algorithm
     (zero equilibrium velocity on wall rows) defaults to on for MRT and off
     for BGK; step2_relax_momentum selects the alternative reading of the
@@ -85,7 +85,7 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_be
         zero_u_at_walls = coll == LB_MRT
     return Params(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom, h_top, coll,
                   int(bool(zero_u_at_walls)), prec, int(bool(walls)),
-                  int(bool(step2_relax_momentum)))
+                  int(bool(step2_relax_momentum)), int(mrt_lut))
 
 
 _lib = None
@@ -138,6 +138,7 @@ def lib():
                 "lb_get_geometry": (i, [_H, i, vp]),
                 "lb_init_channel": (i, [_H, i, i, i, d, d]),
                 "lb_meniscus": (i, [_H, i, i, i, i, i, d, _D, _D, _D]),
+                "lb_set_wetting": (i, [_H, i, d, d]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -263,6 +264,9 @@ class _HandleBase:
         assert cls.shape == (self.nys[dom], self.nxs[dom])
         hc = np.ascontiguousarray(h_class, dtype=np.float64)
         _check(lib().lb_set_geometry(self.h, dom, _np_ptr(cls), hc.ctypes.data_as(_D), len(hc)))
+
+    def set_wetting(self, h_bottom, h_top, dom=0):
+        _check(lib().lb_set_wetting(self.h, dom, float(h_bottom), float(h_top)))
 
     def geometry(self, dom=0):
         cls = np.empty((self.nys[dom], self.nxs[dom]), dtype=np.uint8)

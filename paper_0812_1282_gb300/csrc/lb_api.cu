@@ -154,6 +154,8 @@ int validate(const lb_params* p)
     if (p->walls != 0 && p->walls != 1) return fail(LB_ERR_INVALID_ARG, "walls must be 0 or 1");
     if (p->step2_relax_momentum != 0 && p->step2_relax_momentum != 1)
         return fail(LB_ERR_INVALID_ARG, "step2_relax_momentum must be 0 or 1");
+    if (p->mrt_lut != 0 && (p->mrt_lut < 2 || p->mrt_lut > (1 << 24) || p->collision != LB_MRT))
+        return fail(LB_ERR_INVALID_ARG, "mrt_lut must be 0, or 2..2^24 with LB_MRT");
     return LB_OK;
 }
 
@@ -442,6 +444,13 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.tau_c1 = 0.5 * (p.tau_alpha - p.tau_beta);
         D.h_bot = p.h_bottom;
         D.h_top = p.h_top;
+        D.lut_lo = D.lut_step = D.lut_inv = D.lut_kmax = 0.0;
+        if (p.mrt_lut >= 2 && p.tau_alpha != p.tau_beta) {
+            D.lut_lo = std::min(p.tau_alpha, p.tau_beta);
+            D.lut_step = (std::max(p.tau_alpha, p.tau_beta) - D.lut_lo) / (p.mrt_lut - 1);
+            D.lut_inv = 1.0 / D.lut_step;
+            D.lut_kmax = p.mrt_lut - 1;
+        }
         D.err = h->d_err();
         D.fa = float(D.a);
         D.fkappa = float(D.kappa);
@@ -451,6 +460,10 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.ftau_c1 = float(D.tau_c1);
         D.fh_bot = float(D.h_bot);
         D.fh_top = float(D.h_top);
+        D.flut_lo = float(D.lut_lo);
+        D.flut_step = float(D.lut_step);
+        D.flut_inv = float(D.lut_inv);
+        D.flut_kmax = float(D.lut_kmax);
         D.cls = nullptr;
         D.phi = h->base + L.geo_phi[d];
         for (int k = 0; k < 8; ++k) {
@@ -827,6 +840,28 @@ int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const doubl
                             h->stream));
     LB_CUDA(cudaStreamSynchronize(h->stream));
     return build_items(h);
+}
+
+int lb_set_wetting(lb_handle* h, int dom, double h_bottom, double h_top)
+{
+    int rc = check_dom(h, dom);
+    if (rc != LB_OK) return rc;
+    if (!std::isfinite(h_bottom) || !std::isfinite(h_top))
+        return fail(LB_ERR_INVALID_ARG, "wetting gradients must be finite");
+    DomDesc& D = h->descs[dom];
+    // kernels take the descriptor by value (captured in the step graphs)
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    h->params[dom].h_bottom = h_bottom;
+    h->params[dom].h_top = h_top;
+    D.h_bot = h_bottom;
+    D.h_top = h_top;
+    D.fh_bot = float(h_bottom);
+    D.fh_top = float(h_top);
+    LB_CUDA(cudaMemcpyAsync(h->d_descs() + dom, &D, sizeof(DomDesc), cudaMemcpyHostToDevice,
+                            h->stream));
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    return LB_OK;
 }
 
 int lb_get_geometry(lb_handle* h, int dom, unsigned char* cls)

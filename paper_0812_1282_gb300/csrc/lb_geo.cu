@@ -42,14 +42,16 @@ __device__ __forceinline__ NodeParams<Real> geo_params(const DomDesc& D);
 template <>
 __device__ __forceinline__ NodeParams<float> geo_params<float>(const DomDesc& D)
 {
-    return NodeParams<float>{D.fa,      D.fkappa,  D.fgamma, D.fomega_phi,
-                             D.ftau_c0, D.ftau_c1, D.fh_bot, D.fh_top};
+    return NodeParams<float>{D.fa,      D.fkappa,  D.fgamma,   D.fomega_phi,
+                             D.ftau_c0, D.ftau_c1, D.fh_bot,   D.fh_top,
+                             D.flut_lo, D.flut_step, D.flut_inv, D.flut_kmax};
 }
 template <>
 __device__ __forceinline__ NodeParams<double> geo_params<double>(const DomDesc& D)
 {
-    return NodeParams<double>{D.a,      D.kappa,  D.gamma, D.omega_phi,
-                              D.tau_c0, D.tau_c1, D.h_bot, D.h_top};
+    return NodeParams<double>{D.a,      D.kappa,  D.gamma,   D.omega_phi,
+                              D.tau_c0, D.tau_c1, D.h_bot,   D.h_top,
+                              D.lut_lo, D.lut_step, D.lut_inv, D.lut_kmax};
 }
 
 template <typename Real>

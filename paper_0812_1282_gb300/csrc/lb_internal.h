@@ -27,10 +27,14 @@ struct DomDesc {
     double omega_phi;         // 1 / tau_phi
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)
     double h_bot, h_top;      // wetting gradients
+    // lookup table of Sec. V (lut_kmax = 0: exact tau): tau = lut_lo + k lut_step,
+    // k = nearest integer to (tau - lut_lo) lut_inv, clamped to [0, lut_kmax]
+    double lut_lo, lut_step, lut_inv, lut_kmax;
     unsigned* err;            // device error word (bounded waits that gave up)
     // the same parameters rounded to float once on the host (the FP32 step
     // reads these; converting in the kernel would run on the slow FP64 pipe)
     float fa, fkappa, fgamma, fomega_phi, ftau_c0, ftau_c1, fh_bot, fh_top;
+    float flut_lo, flut_step, flut_inv, flut_kmax;
     // Obstacles (nullptr: none).  cls[y * nx + x] = 0 for a fluid node, k in
     // 1..kMaxClass for a solid node of wetting class k with inward-normal
     // wetting gradient hcls[k].  phi: per-node order parameter written by the

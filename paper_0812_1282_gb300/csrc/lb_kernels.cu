@@ -266,6 +266,7 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
     prm.tau_c1 = D.tau_c1;
     prm.h_bot = D.h_bot;
     prm.h_top = D.h_top;
+    prm.lut_lo = prm.lut_step = prm.lut_inv = prm.lut_kmax = 0.0;  // no collision here
     const long long n = (long long)nx * ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {

@@ -22,6 +22,7 @@ namespace lbfe {
 template <typename Real>
 struct NodeParams {
     Real a, kappa, gamma, omega_phi, tau_c0, tau_c1, h_bot, h_top;
+    Real lut_lo, lut_step, lut_inv, lut_kmax;  // lookup table of Sec. V (kmax 0: off)
 };
 
 template <typename Real>
@@ -243,8 +244,14 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
     const Real jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
     const Real rho = Real(1) + drho;
     const Real irho = rcp_rn(rho);
-    // Eq. (tau); equal phase viscosities give a constant rate
-    const Real omega = P.tau_c1 == Real(0) ? rcp_rn(P.tau_c0) : rcp_rn(P.tau_c0 + P.tau_c1 * phi);
+    // Eq. (tau); equal phase viscosities give a constant rate; with the lookup
+    // table of Sec. V the nearest tabulated tau
+    Real tau = P.tau_c1 == Real(0) ? P.tau_c0 : P.tau_c0 + P.tau_c1 * phi;
+    if (P.lut_kmax > Real(0)) {
+        const Real k = fmin(fmax(rint((tau - P.lut_lo) * P.lut_inv), Real(0)), P.lut_kmax);
+        tau = P.lut_lo + k * P.lut_step;
+    }
+    const Real omega = rcp_rn(tau);
     // Step 2
     Real jxe = jx, jye = jy, uxe = jx * irho, uye = jy * irho;
     if (step2) {

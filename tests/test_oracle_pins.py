@@ -617,3 +617,43 @@ def test_step_window_matches_full_step(oracle_mod):
         fo, go = oracle_mod.step_window(p, nx, ny, b0, f0[:, b0:b1], g0[:, b0:b1], x0, x1, y0, y1)
         assert np.array_equal(fo, lat.f[:, y0:y1, x0:x1])
         assert np.array_equal(go, lat.g[:, y0:y1, x0:x1])
+
+
+# ------------------------------------------------- lookup-table MRT, Sec. V
+def test_lookup_table_tau(oracle_mod):
+    """Sec. V replaces the per-node collision matrix by the nearest of ~1e4
+    tabulated viscosities: tau takes exactly n values, the bulk values at the
+    table ends, within half a table step of Eq. (tau) inside [-1, 1],
+    monotone in phi, clamped beyond the bulk values; BGK ignores the table."""
+    for ta, tb in ((3.0, 0.7), (0.6, 1.5)):
+        n = 101
+        p = oracle_mod.params(collision="mrt", tau_alpha=ta, tau_beta=tb, mrt_lut=n)
+        exact = oracle_mod.params(collision="mrt", tau_alpha=ta, tau_beta=tb)
+        step = abs(ta - tb) / (n - 1)
+        assert oracle_mod.node_tau(p, 1.0) == ta and oracle_mod.node_tau(p, -1.0) == tb
+        phis = np.linspace(-1.0, 1.0, 20001)
+        taus = np.array([oracle_mod.node_tau(p, v) for v in phis])
+        ex = np.array([oracle_mod.node_tau(exact, v) for v in phis])
+        assert np.abs(taus - ex).max() <= step / 2 + 1e-13
+        assert len(np.unique(np.round(taus, 12))) == n
+        d = np.diff(taus) * np.sign(ta - tb)
+        assert (d >= -1e-15).all()
+        assert oracle_mod.node_tau(p, 1.3) == oracle_mod.node_tau(p, 1.0)
+        assert oracle_mod.node_tau(p, -1.3) == oracle_mod.node_tau(p, -1.0)
+        bgk = oracle_mod.params(collision="bgk", tau_alpha=ta, tau_beta=tb, mrt_lut=n)
+        assert oracle_mod.node_tau(bgk, 0.3) == oracle_mod.node_tau(exact, 0.3)
+
+
+def test_lookup_table_run_converges_to_exact(oracle_mod):
+    """A 1e4-entry table changes a drop run by far less than a coarse one."""
+    nx, ny = 48, 24
+    kw = dict(collision="mrt", tau_alpha=3.0, tau_beta=0.7, h_bottom=oracle_mod.wetting_h(70.0))
+    runs = {}
+    for n in (0, 10000, 3):
+        lat = oracle_mod.OracleLattice(oracle_mod.params(mrt_lut=n, **kw), nx, ny)
+        lat.init_drop(10.0, 24.0, -0.5)
+        lat.step(400)
+        runs[n] = lat.moments()[1]
+    fine = np.abs(runs[10000] - runs[0]).max()
+    coarse = np.abs(runs[3] - runs[0]).max()
+    assert fine < 1e-3 and coarse > 20 * fine
