@@ -413,6 +413,14 @@ def ours(args):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
 
+    if args.only:
+        # one extra workload alone (profiling aid): its JSON object only
+        if args.only == "batched":
+            res = run_batched(lbf, torch, max(4, args.steps))
+        else:
+            res = run_capillary(lbf, torch, max(1000, args.steps))
+        print(json.dumps({"workload": args.only, **res}), flush=True)
+        return
     tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
     with ClockSampler(torch.cuda.current_device()) as clk:
         sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup, size=args.size, tile=tile)
@@ -575,6 +583,8 @@ def main():
                     help="side of a smaller square lattice (profiling aid; default 8192)")
     ap.add_argument("--tile", default=None,
                     help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
+    ap.add_argument("--only", choices=("batched", "capillary"), default=None,
+                    help="run one extra workload alone for --steps steps (profiling aid)")
     ap.add_argument("--experiment", choices=("ramp",), default=None,
                     help="run a physics experiment instead of the benchmark and print its "
                          "JSON table (ramp: the quasi-static wetting ramp of Sec. IV)")
