@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbfe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lb_kernels.cu", "lb_api.cu", "lb_noalloc.cu", "lb_geo.cu"]
+SOURCES = ["lb_kernels.cu", "lb_api.cu", "lb_noalloc.cu", "lb_geo.cu", "lb_step_f32.cu",
+           "lb_step_f64.cu"]
 
 
 def nvcc() -> str:

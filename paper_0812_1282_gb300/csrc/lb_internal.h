@@ -92,6 +92,16 @@ int launch_geo_solid_rest(int precision, const DomDesc& d, int b, void* stream);
 // device before the first launch, outside any stream capture).
 int prepare_step_kernels();
 
+// Per-precision halves of launch_step / prepare_step_kernels.
+int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
+                    void* stream);
+int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
+                    void* stream);
+int prepare_step_f32();
+int prepare_step_f64();
+
 // Dynamic shared memory of the step kernel for a block width (0 if the
 // width is not supported for this precision).
 size_t step_smem_bytes(int precision, int block_x);

@@ -6,86 +6,13 @@
 
 #include "lb_internal.h"
 #include "lb_node.cuh"
-#include "lb_step.cuh"
+#include "lb_step_kernels.cuh"
 
 namespace lbfe {
 
 // ------------------------------------------------------------------ step
-// Stage-ring depth: rows of bulk copies in flight per CTA.
-template <typename Real>
-constexpr int kStages = sizeof(Real) == 4 ? 4 : 3;
-
-// Launch shape: blockDim.x = W + 32 (one producer warp, W / 32 compute
-// warps), W the strip width.
-template <typename Real, bool MRT>
-__global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity, int rows)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int S = kStages<Real>;
-    const int NW = int(blockDim.x >> 5) - 1;
-    init_stages<Real, S>(smem, NW);
-    const int warp = int(threadIdx.x >> 5);
-    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
-    unsigned q = 0;
-    if (warp == 0) {
-        produce_tile<Real, S>(D, parity, x0, y0, rows, smem, NW, q);
-        drain_stages<Real, S>(smem, NW, q, D.err);
-    } else {
-        consume_tile<Real, MRT, S>(D, parity, x0, y0, rows, smem, NW, warp - 1, q);
-    }
-}
-
-// Persistent form: a fixed grid walks a list of tiles of many domains.  The
-// producer warp takes the next tile from a device counter (dynamic load
-// balance: tiles differ in size) and names it to the compute warps through
-// the tile's first stage slot; the stage ring carries over from tile to
-// tile.  sched[0] is the tile counter, sched[1] counts finished CTAs; the
-// last CTA to finish resets both for the next launch.
-template <typename Real, bool MRT>
-__global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restrict__ descs,
-                                                         const WorkItem* __restrict__ items,
-                                                         int n_items, int parity, int* sched,
-                                                         unsigned* err)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int tags[kStages<Real>];
-    constexpr int S = kStages<Real>;
-    const int NW = int(blockDim.x >> 5) - 1;
-    init_stages<Real, S>(smem, NW);
-    const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
-    unsigned q = 0;
-    if (warp == 0) {
-        for (;;) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(sched, 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= n_items) {
-                produce_end<Real, S>(smem, NW, q, tags, err);
-                break;
-            }
-            const WorkItem w = items[it];
-            const DomDesc D = descs[w.dom];
-            produce_tile<Real, S>(D, parity, w.x0, w.y0, w.rows, smem, NW, q, tags, it);
-        }
-        drain_stages<Real, S>(smem, NW, q, err);
-        if (lane == 0) {
-            __threadfence();
-            if (atomicAdd(sched + 1, 1) == int(gridDim.x) - 1) {  // last CTA: reset
-                sched[0] = 0;
-                sched[1] = 0;
-                __threadfence();
-            }
-        }
-    } else {
-        for (;;) {
-            const int it = next_tag<Real, S>(smem, NW, q, tags, err);
-            if (it < 0 || it >= n_items) break;  // end of the list (or a failed wait)
-            const WorkItem w = items[it];
-            const DomDesc D = descs[w.dom];
-            consume_tile<Real, MRT, S>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
-        }
-    }
-}
+// The step kernels live in lb_step_kernels.cuh, instantiated per precision in
+// lb_step_f32.cu and lb_step_f64.cu (compiled in parallel).
 
 size_t step_smem_bytes(int precision, int bx)
 {
@@ -94,43 +21,11 @@ size_t step_smem_bytes(int precision, int bx)
                           : StageLayout<double>(bx / 32, kStages<double>).total();
 }
 
-template <typename Real, bool MRT>
-static cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                                 int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
-                                 int* sched, cudaStream_t s)
-{
-    const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
-    const int threads = bx + 32;
-    if (n_dom == 1 && d_items == nullptr) {
-        dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
-        step_single_kernel<Real, MRT><<<grid, threads, smem, s>>>(d, parity, rows);
-    } else {
-        const int grid = grid_p > 0 ? grid_p : n_items;
-        step_batch_kernel<Real, MRT><<<grid, threads, smem, s>>>(d_descs, d_items, n_items, parity,
-                                                                 sched, d.err);
-    }
-    return cudaGetLastError();
-}
-
-template <typename Real, bool MRT>
-static cudaError_t allow_large_smem()
-{
-    const int bytes = 200 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(step_single_kernel<Real, MRT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step_batch_kernel<Real, MRT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
 int prepare_step_kernels()
 {
-    cudaError_t e = allow_large_smem<float, false>();
-    if (e == cudaSuccess) e = allow_large_smem<float, true>();
-    if (e == cudaSuccess) e = allow_large_smem<double, false>();
-    if (e == cudaSuccess) e = allow_large_smem<double, true>();
-    return static_cast<int>(e);
+    int e = prepare_step_f32();
+    if (e == 0) e = prepare_step_f64();
+    return e;
 }
 
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
@@ -138,20 +33,11 @@ int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_desc
                 int grid_persistent, int* sched, void* stream)
 {
     if (step_smem_bytes(precision, block_x) == 0) return int(cudaErrorInvalidValue);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (precision == 0) {
-        e = coll ? launch_step_t<float, true>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
-                                              rows, grid_persistent, sched, s)
-                 : launch_step_t<float, false>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
-                                               rows, grid_persistent, sched, s);
-    } else {
-        e = coll ? launch_step_t<double, true>(d, d_descs, d_items, n_items, n_dom, parity, block_x,
-                                               rows, grid_persistent, sched, s)
-                 : launch_step_t<double, false>(d, d_descs, d_items, n_items, n_dom, parity,
-                                                block_x, rows, grid_persistent, sched, s);
-    }
-    return static_cast<int>(e);
+    return precision == 0
+               ? launch_step_f32(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
+                                 grid_persistent, sched, stream)
+               : launch_step_f64(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
+                                 grid_persistent, sched, stream);
 }
 
 // Periodic ghost columns of every row of the 18 planes of one buffer, from

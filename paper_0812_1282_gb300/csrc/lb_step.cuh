@@ -120,11 +120,12 @@ struct TileRows {
 // ----------------------------------------------------------- producer
 // Warp 0: issue the stages of one tile.  q counts the stages this CTA has
 // issued so far (it continues across tiles of a persistent CTA).
-template <typename Real, int S>
+template <typename Real, int S, int NWC = 0>
 __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             unsigned char* __restrict__ smem, int NW, unsigned& q,
+                                             unsigned char* __restrict__ smem, int nw, unsigned& q,
                                              int* tags = nullptr, int tag = 0)
 {
+    const int NW = NWC > 0 ? NWC : nw;  // compile-time strip width when specialised
     const Real* __restrict__ fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
     const Real* __restrict__ gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
     const int ny = D.ny, pitch = D.pitch;
@@ -181,11 +182,12 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
 // ----------------------------------------------------------- consumer
 // Compute warp cw (0-based among compute warps) processes its 32 columns of
 // one tile.  q: stage sequence number of the tile's first stage.
-template <typename Real, bool MRT, int S>
+template <typename Real, bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
-                                             unsigned char* __restrict__ smem, int NW, int cw,
+                                             unsigned char* __restrict__ smem, int nw, int cw,
                                              unsigned& q)
 {
+    const int NW = NWC > 0 ? NWC : nw;  // compile-time strip width when specialised
     Real* __restrict__ fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
     Real* __restrict__ gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
     const int nx = D.nx, ny = D.ny, pitch = D.pitch;
@@ -330,10 +332,11 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
 
 // Producer: the work list is exhausted; complete the next stage slot with
 // no bytes and the tag -1, which tells the compute warps to stop.
-template <typename Real, int S>
-__device__ __forceinline__ void produce_end(unsigned char* smem, int NW, unsigned& q, int* tags,
+template <typename Real, int S, int NWC = 0>
+__device__ __forceinline__ void produce_end(unsigned char* smem, int nw, unsigned& q, int* tags,
                                             unsigned* err)
 {
+    const int NW = NWC > 0 ? NWC : nw;
     const StageLayout<Real> L(NW, S);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
@@ -348,19 +351,21 @@ __device__ __forceinline__ void produce_end(unsigned char* smem, int NW, unsigne
 }
 
 // Compute warps: wait for the first stage of the next tile and read its tag.
-template <typename Real, int S>
-__device__ __forceinline__ int next_tag(unsigned char* smem, int NW, unsigned q, const int* tags,
+template <typename Real, int S, int NWC = 0>
+__device__ __forceinline__ int next_tag(unsigned char* smem, int nw, unsigned q, const int* tags,
                                         unsigned* err)
 {
+    const int NW = NWC > 0 ? NWC : nw;
     const StageLayout<Real> L(NW, S);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     if (!mbar_wait(full + (q % unsigned(S)), (q / unsigned(S)) & 1u, err)) return -1;
     return *reinterpret_cast<const volatile int*>(tags + (q % unsigned(S)));
 }
 
-template <typename Real, int S>
-__device__ __forceinline__ void init_stages(unsigned char* smem, int NW)
+template <typename Real, int S, int NWC = 0>
+__device__ __forceinline__ void init_stages(unsigned char* smem, int nw)
 {
+    const int NW = NWC > 0 ? NWC : nw;
     const StageLayout<Real> L(NW, S);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
@@ -377,10 +382,11 @@ __device__ __forceinline__ void init_stages(unsigned char* smem, int NW)
 // Before the producer warp exits, every bulk copy it issued must have
 // landed (they all have unless a wait timed out; this bounded wait covers
 // that case).
-template <typename Real, int S>
-__device__ __forceinline__ void drain_stages(unsigned char* smem, int NW, unsigned q,
+template <typename Real, int S, int NWC = 0>
+__device__ __forceinline__ void drain_stages(unsigned char* smem, int nw, unsigned q,
                                              unsigned* err)
 {
+    const int NW = NWC > 0 ? NWC : nw;
     if (threadIdx.x != 0 || q == 0) return;
     const StageLayout<Real> L(NW, S);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());

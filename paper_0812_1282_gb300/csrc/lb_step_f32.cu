@@ -1,0 +1,16 @@
+// FP32 instantiation of the fused step kernels (see lb_step_kernels.cuh).
+#include "lb_step_kernels.cuh"
+
+namespace lbfe {
+
+int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
+                    void* stream)
+{
+    return launch_step_prec<float>(coll, d, d_descs, d_items, n_items, n_dom, parity, bx, rows,
+                                   grid_p, sched, stream);
+}
+
+int prepare_step_f32() { return prepare_step_prec<float>(); }
+
+}  // namespace lbfe

@@ -1,0 +1,172 @@
+// Fused step kernels (single domain and batched work list) and their
+// launchers, templated on precision, collision and the strip width.
+//
+// The strip width W = 32 NW is a template constant (NWC = NW) for the three
+// widths the autotuner uses (64, 128, 256 columns), so every shared-memory
+// offset of the stage ring and the phi rings folds into an immediate; other
+// widths (multiples of 32 up to 256) take the generic form (NWC = 0, width
+// read from blockDim).  Both forms run the same code on the same data.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lb_internal.h"
+#include "lb_step.cuh"
+
+namespace lbfe {
+
+// Stage-ring depth: rows of bulk copies in flight per CTA.
+template <typename Real>
+constexpr int kStages = sizeof(Real) == 4 ? 4 : 3;
+
+// Launch shape: blockDim.x = W + 32 (one producer warp, W / 32 compute
+// warps), W the strip width.
+template <typename Real, bool MRT, int NWC>
+__global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity, int rows)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStages<Real>;
+    const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
+    init_stages<Real, S, NWC>(smem, NW);
+    const int warp = int(threadIdx.x >> 5);
+    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
+    unsigned q = 0;
+    if (warp == 0) {
+        produce_tile<Real, S, NWC>(D, parity, x0, y0, rows, smem, NW, q);
+        drain_stages<Real, S, NWC>(smem, NW, q, D.err);
+    } else {
+        consume_tile<Real, MRT, S, NWC>(D, parity, x0, y0, rows, smem, NW, warp - 1, q);
+    }
+}
+
+// Persistent form: a fixed grid walks a list of tiles of many domains.  The
+// producer warp takes the next tile from a device counter (dynamic load
+// balance: tiles differ in size) and names it to the compute warps through
+// the tile's first stage slot; the stage ring carries over from tile to
+// tile.  sched[0] is the tile counter, sched[1] counts finished CTAs; the
+// last CTA to finish resets both for the next launch.
+template <typename Real, bool MRT, int NWC>
+__global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restrict__ descs,
+                                                         const WorkItem* __restrict__ items,
+                                                         int n_items, int parity, int* sched,
+                                                         unsigned* err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int tags[kStages<Real>];
+    constexpr int S = kStages<Real>;
+    const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
+    init_stages<Real, S, NWC>(smem, NW);
+    const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    unsigned q = 0;
+    if (warp == 0) {
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(sched, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n_items) {
+                produce_end<Real, S, NWC>(smem, NW, q, tags, err);
+                break;
+            }
+            const WorkItem w = items[it];
+            const DomDesc D = descs[w.dom];
+            produce_tile<Real, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, q, tags, it);
+        }
+        drain_stages<Real, S, NWC>(smem, NW, q, err);
+        if (lane == 0) {
+            __threadfence();
+            if (atomicAdd(sched + 1, 1) == int(gridDim.x) - 1) {  // last CTA: reset
+                sched[0] = 0;
+                sched[1] = 0;
+                __threadfence();
+            }
+        }
+    } else {
+        for (;;) {
+            const int it = next_tag<Real, S, NWC>(smem, NW, q, tags, err);
+            if (it < 0 || it >= n_items) break;  // end of the list (or a failed wait)
+            const WorkItem w = items[it];
+            const DomDesc D = descs[w.dom];
+            consume_tile<Real, MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
+        }
+    }
+}
+
+template <typename Real, bool MRT, int NWC>
+cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                          int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
+                          int* sched, cudaStream_t s)
+{
+    const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
+    const int threads = bx + 32;
+    if (n_dom == 1 && d_items == nullptr) {
+        dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
+        step_single_kernel<Real, MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows);
+    } else {
+        const int grid = grid_p > 0 ? grid_p : n_items;
+        step_batch_kernel<Real, MRT, NWC><<<grid, threads, smem, s>>>(d_descs, d_items, n_items,
+                                                                      parity, sched, d.err);
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real, bool MRT>
+cudaError_t launch_step_w(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                          int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
+                          int* sched, cudaStream_t s)
+{
+    switch (bx) {
+        case 64:
+            return launch_step_t<Real, MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                               rows, grid_p, sched, s);
+        case 128:
+            return launch_step_t<Real, MRT, 4>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                               rows, grid_p, sched, s);
+        case 256:
+            return launch_step_t<Real, MRT, 8>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                               rows, grid_p, sched, s);
+        default:
+            return launch_step_t<Real, MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                               rows, grid_p, sched, s);
+    }
+}
+
+template <typename Real>
+int launch_step_prec(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
+                     int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
+                     void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return int(coll ? launch_step_w<Real, true>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                rows, grid_p, sched, s)
+                    : launch_step_w<Real, false>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s));
+}
+
+// Opt every instantiation in to large dynamic shared memory.
+template <typename Real, bool MRT, int NWC>
+cudaError_t allow_large_smem_one()
+{
+    const int bytes = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(step_single_kernel<Real, MRT, NWC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_batch_kernel<Real, MRT, NWC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+template <typename Real>
+int prepare_step_prec()
+{
+    cudaError_t e = cudaSuccess;
+    const cudaError_t r[] = {
+        allow_large_smem_one<Real, false, 0>(), allow_large_smem_one<Real, false, 2>(),
+        allow_large_smem_one<Real, false, 4>(), allow_large_smem_one<Real, false, 8>(),
+        allow_large_smem_one<Real, true, 0>(),  allow_large_smem_one<Real, true, 2>(),
+        allow_large_smem_one<Real, true, 4>(),  allow_large_smem_one<Real, true, 8>()};
+    for (cudaError_t v : r)
+        if (v != cudaSuccess) e = v;
+    return int(e);
+}
+
+}  // namespace lbfe
