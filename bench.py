@@ -184,11 +184,12 @@ def time_steps(sim, steps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", size=None, tile=None):
+def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", size=None, tile=None,
+                 compact=False):
     c = lbinputs.SPINODAL_8192
     nx = ny = size or c["nx"]
     n = nx * ny
-    p = lbf.params(precision=precision, **c["params"])
+    p = lbf.params(precision=precision, compact_g=compact, **c["params"])
     sim = lbf.Lattice(p, nx, ny)
     sim.init_random(c["amp"], c["seed"])
     if tile:
@@ -429,7 +430,8 @@ def ours(args):
         return
     tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
     with ClockSampler(torch.cuda.current_device()) as clk:
-        sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup, size=args.size, tile=tile)
+        sim, head = run_headline(lbf, torch, ws, args.steps, args.warmup, size=args.size, tile=tile,
+                                 compact=args.storage == "compact")
     clocks = clk.summary()
     sim.close()
     torch.cuda.empty_cache()
@@ -589,6 +591,8 @@ def main():
                     help="side of a smaller square lattice (profiling aid; default 8192)")
     ap.add_argument("--tile", default=None,
                     help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
+    ap.add_argument("--storage", choices=("full", "compact"), default="full",
+                    help="g storage of the headline lattice (compact: phi, Gamma mu, u_eq)")
     ap.add_argument("--only", choices=("batched", "capillary"), default=None,
                     help="run one extra workload alone for --steps steps (profiling aid)")
     ap.add_argument("--experiment", choices=("ramp",), default=None,

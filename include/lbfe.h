@@ -76,6 +76,14 @@ typedef struct lb_params {
                             every node; n >= 2 uses the nearest of n viscosities spaced
                             evenly between tau_beta and tau_alpha (ends included, the end
                             values beyond them): the lookup table of Sec. V            */
+    int compact_g;       /* 1: store g compactly (FP32 and tau_phi = 1 only; no obstacles).
+                            With tau_phi = 1 the post-collision g of a node is its
+                            equilibrium (Eq. gevo), fixed by phi, Gamma mu and u_eq, so the
+                            state keeps those four numbers instead of nine g values:
+                            104 instead of 144 bytes of traffic per node update.  The
+                            scheme is the same; g'_0 = phi - sum g'_i is implicit.
+                            lb_set_populations is not available on such a handle.
+                            Default 0. */
 } lb_params;
 
 /* Diagnostics of one domain (sums over all nodes, in FP64). */

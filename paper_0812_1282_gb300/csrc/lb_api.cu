@@ -156,6 +156,10 @@ int validate(const lb_params* p)
         return fail(LB_ERR_INVALID_ARG, "step2_relax_momentum must be 0 or 1");
     if (p->mrt_lut != 0 && (p->mrt_lut < 2 || p->mrt_lut > (1 << 24) || p->collision != LB_MRT))
         return fail(LB_ERR_INVALID_ARG, "mrt_lut must be 0, or 2..2^24 with LB_MRT");
+    if (p->compact_g != 0 && p->compact_g != 1)
+        return fail(LB_ERR_INVALID_ARG, "compact_g must be 0 or 1");
+    if (p->compact_g && (p->precision != LB_FP32 || p->tau_phi != 1.0))
+        return fail(LB_ERR_INVALID_ARG, "compact_g needs LB_FP32 and tau_phi = 1");
     return LB_OK;
 }
 
@@ -363,8 +367,11 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
     for (int d = 0; d < n_dom; ++d) {
         const int rc = validate(&per_dom[d]);
         if (rc != LB_OK) return rc;
-        if (per_dom[d].precision != per_dom[0].precision || per_dom[d].collision != per_dom[0].collision)
-            return fail(LB_ERR_INVALID_ARG, "precision and collision must match across a batch");
+        if (per_dom[d].precision != per_dom[0].precision ||
+            per_dom[d].collision != per_dom[0].collision ||
+            per_dom[d].compact_g != per_dom[0].compact_g)
+            return fail(LB_ERR_INVALID_ARG,
+                        "precision, collision and compact_g must match across a batch");
         if (nx[d] < 3 || ny[d] < 3) return fail(LB_ERR_INVALID_ARG, "domain %d smaller than 3x3", d);
     }
     Layout L;
@@ -436,6 +443,7 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.walls = p.walls;
         D.step2 = p.zero_u_at_walls ? 1 : 0;
         D.step2_relax_j = p.step2_relax_momentum ? 1 : 0;
+        D.compact = p.compact_g ? 1 : 0;
         D.a = p.a;
         D.kappa = p.kappa;
         D.gamma = p.gamma_mob;
@@ -808,6 +816,8 @@ int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const doubl
     int rc = check_dom(h, dom);
     if (rc != LB_OK) return rc;
     DomDesc& D = h->descs[dom];
+    if (cls && D.compact)
+        return fail(LB_ERR_INVALID_ARG, "obstacles need the full g storage (compact_g = 0)");
     if (cls) {
         if (!h_class || n_class < 1 || n_class > lbfe::kMaxClass + 1)
             return fail(LB_ERR_INVALID_ARG, "h_class must hold 1..%d entries", lbfe::kMaxClass + 1);
@@ -995,9 +1005,40 @@ int lb_get_populations_rows(lb_handle* h, int dom, int y0, int nrows, double* f,
     if (y0 < 0 || nrows < 1 || y0 + nrows > D.ny) return fail(LB_ERR_INVALID_ARG, "bad row range");
     const size_t nn = size_t(D.nx) * nrows, es = h->elem();
     std::vector<unsigned char> tmp(nn * es);
+    if (D.compact && g) {
+        // g' from the compact state: g'_i = g^eq_i(phi, Gamma mu, u_eq) for
+        // i > 0 (Appendix A), g'_0 = phi - sum_{i>0} g'_i
+        std::vector<float> c(4 * nn);
+        for (int k = 0; k < 4; ++k) {
+            const unsigned char* plane = static_cast<const unsigned char*>(D.g[h->parity]) +
+                                         (size_t(k) * D.plane + size_t(y0) * D.pitch + lbfe::kXOff) * es;
+            LB_CUDA(cudaMemcpy2DAsync(c.data() + k * nn, es * D.nx, plane, es * D.pitch,
+                                      es * D.nx, nrows, cudaMemcpyDeviceToHost, h->stream));
+        }
+        LB_CUDA(cudaStreamSynchronize(h->stream));
+        for (size_t q = 0; q < nn; ++q) {
+            const double phi = lbfe::G0<float>::decode(c[q]);
+            const double G = c[nn + q], ux = c[2 * nn + q], uy = c[3 * nn + q];
+            const double pux = phi * ux, puy = phi * uy;
+            const double pxx = pux * ux, pyy = puy * uy, pxy = pux * uy, puu = pxx + pyy;
+            const double Cx = 4 * G + 6 * pxx - 2 * puu, Cy = 4 * G + 6 * pyy - 2 * puu;
+            const double Cd = G + puu + 3 * pxy, Ca = G + puu - 3 * pxy;
+            const double ge[9] = {0.0,
+                                  (Cx + 4 * pux) / 12, (Cx - 4 * pux) / 12,
+                                  (Cy + 4 * puy) / 12, (Cy - 4 * puy) / 12,
+                                  (Cd + (pux + puy)) / 12, (Cd - (pux + puy)) / 12,
+                                  (Ca + (puy - pux)) / 12, (Ca - (puy - pux)) / 12};
+            double tail = 0.0;
+            for (int i = 1; i < 9; ++i) {
+                g[i * nn + q] = ge[i];
+                tail += ge[i];
+            }
+            g[q] = phi - tail;
+        }
+    }
     for (int which = 0; which < 2; ++which) {
         double* out = which == 0 ? f : g;
-        if (!out) continue;
+        if (!out || (which == 1 && D.compact)) continue;
         const unsigned char* src =
             static_cast<const unsigned char*>(which == 0 ? D.f[h->parity] : D.g[h->parity]);
         for (int i = 0; i < 9; ++i) {
@@ -1036,6 +1077,10 @@ int lb_set_populations(lb_handle* h, int dom, const double* f, const double* g)
     if (rc != LB_OK) return rc;
     if (!f || !g) return fail(LB_ERR_INVALID_ARG, "f and g are required");
     const DomDesc& D = h->descs[dom];
+    if (D.compact)
+        return fail(LB_ERR_INVALID_ARG,
+                    "a compact-g handle holds only equilibrium g; set its state with lb_init_* "
+                    "or lb_load_state");
     const size_t nn = size_t(D.nx) * D.ny, es = h->elem();
     std::vector<unsigned char> tmp(9 * nn * es);
     for (int which = 0; which < 2; ++which) {

@@ -23,6 +23,8 @@ struct DomDesc {
     int walls;         // 1: bounce-back walls below row 0 and above row ny-1
     int step2;         // zero equilibrium velocity on wall rows (Sec. V, Step 2)
     int step2_relax_j; // MRT: relax wall-row momentum at rate 1 (alternative reading)
+    int compact;       // FP32, tau_phi = 1: g stored as (phi word, Gamma mu, u_eq) in
+                       // g planes 0..3 (lb_step_compact.cuh)
     double a, kappa, gamma;   // free energy and mobility parameters
     double omega_phi;         // 1 / tau_phi
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)
@@ -101,6 +103,7 @@ int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
                     void* stream);
 int prepare_step_f32();
 int prepare_step_f64();
+size_t step_smem_bytes_compact(int bx);
 
 // Dynamic shared memory of the step kernel for a block width (0 if the
 // width is not supported for this precision).

@@ -186,9 +186,15 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
         ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
         const long long o = (long long)y * pitch + x + kXOff;
         const long long og1 = x < 2 ? o + nx : -1, og2 = x >= nx - 2 ? o - nx : -1;
+        // compact g storage: (phi word, Gamma mu, u_eq = 0) in planes 0..3
+        const double cg[4] = {0.0, gamma_mu<double>(prm, phi, lap), 0.0, 0.0};
         for (int i = 0; i < 9; ++i) {
             const Real fv = Real(fe[i]);
-            const Real gv = i == 0 ? G0<Real>::encode(ge[0]) : Real(ge[i]);
+            Real gv;
+            if (D.compact)
+                gv = i == 0 ? G0<Real>::encode(phi) : Real(i < 4 ? cg[i] : 0.0);
+            else
+                gv = i == 0 ? G0<Real>::encode(ge[0]) : Real(ge[i]);
             fd[i * P + o] = fv;
             gd[i * P + o] = gv;
             if (og1 >= 0) {
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
         double f[9], g[9];
         for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
         g[0] = G0<Real>::decode(gs[o]);
-        for (int i = 1; i < 9; ++i) g[i] = double(gs[i * P + o]);
+        for (int i = 1; i < 9; ++i) g[i] = D.compact ? 0.0 : double(gs[i * P + o]);
         const double drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
         const double jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
         const double jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
@@ -364,8 +370,10 @@ int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nr
 // touch a solid node are skipped.  Points are appended in arbitrary order;
 // the host sorts them.
 template <typename Real>
-__device__ __forceinline__ double phi_at_node(const Real* g, long long P, long long o)
+__device__ __forceinline__ double phi_at_node(const Real* g, long long P, long long o,
+                                              bool compact)
 {
+    if (compact) return G0<Real>::decode(g[o]);  // the phi word itself
     double v[9];
     v[0] = G0<Real>::decode(g[o]);
     for (int i = 1; i < 9; ++i) v[i] = double(g[i * P + o]);
@@ -384,9 +392,10 @@ __global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count,
         const int y = int(k / nx), x = int(k - (long long)y * nx);
         const unsigned char* cls = D.cls;
         if (cls && cls[k] != 0) continue;  // links touching a solid node carry no interface
-        const double a = phi_at_node(gs, P, (long long)y * pitch + x + kXOff);
+        const bool cmp = D.compact != 0;
+        const double a = phi_at_node(gs, P, (long long)y * pitch + x + kXOff, cmp);
         const int xp = x + 1 == nx ? 0 : x + 1;
-        const double b = phi_at_node(gs, P, (long long)y * pitch + xp + kXOff);
+        const double b = phi_at_node(gs, P, (long long)y * pitch + xp + kXOff, cmp);
         const bool bfluid = !cls || cls[(long long)y * nx + xp] == 0;
         if (bfluid && ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0))) {
             const int idx = atomicAdd(count, 1);
@@ -396,7 +405,7 @@ __global__ void crossings_kernel(DomDesc D, int parity, double* pts, int* count,
             }
         }
         if (y + 1 < ny && (!cls || cls[(long long)(y + 1) * nx + x] == 0)) {
-            const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x + kXOff);
+            const double c = phi_at_node(gs, P, (long long)(y + 1) * pitch + x + kXOff, cmp);
             if ((a > 0.0 && c < 0.0) || (a < 0.0 && c > 0.0)) {
                 const int idx = atomicAdd(count, 1);
                 if (idx < cap) {

@@ -166,10 +166,10 @@ __device__ __forceinline__ void stencils<double>(double c, double e, double w, d
 // Matrix): (fe1 + fe2) - (fe3 + fe4) = rho(ux^2 - uy^2) + kappa(dx^2 - dy^2) and
 // (fe5 + fe6) - (fe7 + fe8) = rho ux uy + kappa dx dy.
 template <typename Real>
-__device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
-                                           Real jxe, Real jye, Real uxe, Real uye, Real dx,
-                                           Real dy, Real lap, Real (&fe)[9], Real (&ge)[9],
-                                           Real& m7eq, Real& m8eq)
+__device__ __forceinline__ void f_equilibria(const NodeParams<Real>& P, Real drho, Real phi,
+                                             Real jxe, Real jye, Real uxe, Real uye, Real dx,
+                                             Real dy, Real lap, Real (&fe)[9], Real& m7eq,
+                                             Real& m8eq)
 {
     const Real phi2 = phi * phi;
     // 3 x isotropic part: 3 [p0 - kappa phi lap] - rho (Eq. p0 minus the rest pressure)
@@ -196,9 +196,21 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
     fe[6] = div_const<36>(Bd - Real(3) * (jxe + jye));
     fe[7] = div_const<36>(Ba + Real(3) * (jye - jxe));
     fe[8] = div_const<36>(Ba - Real(3) * (jye - jxe));
-    // g: w_i [Gamma mu + phi e.u + 3/2 phi (e.u e.u - u.u/3)], times 12
-    const Real mu = P.a * (phi2 * phi - phi) - P.kappa * lap;  // Eq. (chempot)
-    const Real G = P.gamma * mu;
+}
+
+// Gamma mu with the chemical potential of Eq. (chempot).
+template <typename Real>
+__device__ __forceinline__ Real gamma_mu(const NodeParams<Real>& P, Real phi, Real lap)
+{
+    const Real mu = P.a * (phi * phi * phi - phi) - P.kappa * lap;
+    return P.gamma * mu;
+}
+
+// g equilibria for i = 1..8 from phi, G = Gamma mu and the equilibrium
+// velocity: w_i [G + phi e.u + 3/2 phi (e.u e.u - u.u/3)], times 12.
+template <typename Real>
+__device__ __forceinline__ void g_equilibria(Real phi, Real G, Real uxe, Real uye, Real (&ge)[9])
+{
     const Real pux = phi * uxe, puy = phi * uye;
     const Real pxx = pux * uxe, pyy = puy * uye, pxy = pux * uye;
     const Real puu = pxx + pyy;
@@ -214,6 +226,16 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
     ge[6] = div_const<12>(Cd - (pux + puy));
     ge[7] = div_const<12>(Ca + (puy - pux));
     ge[8] = div_const<12>(Ca - (puy - pux));
+}
+
+template <typename Real>
+__device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
+                                           Real jxe, Real jye, Real uxe, Real uye, Real dx,
+                                           Real dy, Real lap, Real (&fe)[9], Real (&ge)[9],
+                                           Real& m7eq, Real& m8eq)
+{
+    f_equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, m7eq, m8eq);
+    g_equilibria<Real>(phi, gamma_mu<Real>(P, phi, lap), uxe, uye, ge);
 }
 
 // One node of Steps 1-3 (Sec. V): moments of the pulled populations f, g
@@ -232,11 +254,13 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
 // with m_7 = d1+d2-d3-d4, m_8 = d5+d6-d7-d8, d = f - f^eq.  With
 // step2_relax_j the momentum rows of a Step-2 node relax at rate 1 instead
 // (the dj terms vanish and the node leaves the collision at rest).
+// The f part of Steps 1-3 at one node: returns the post-collision f and,
+// for the g update, the equilibrium velocity (zero at Step-2 nodes).
 template <typename Real, bool MRT>
-__device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&f)[9],
-                                        const Real (&g)[9], Real phi, Real dx, Real dy, Real lap,
-                                        bool step2, bool step2_relax_j, Real (&fo)[9],
-                                        Real (&go)[9])
+__device__ __forceinline__ void collide_f(const NodeParams<Real>& P, const Real (&f)[9], Real phi,
+                                          Real dx, Real dy, Real lap, bool step2,
+                                          bool step2_relax_j, Real (&fo)[9], Real& uxe_out,
+                                          Real& uye_out)
 {
     // Step 1 (Eq. moments); t_i e_i sums to zero, so deviations give j directly
     const Real drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
@@ -260,8 +284,8 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         uxe = Real(0);
         uye = Real(0);
     }
-    Real fe[9], ge[9], m7eq, m8eq;
-    equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, ge, m7eq, m8eq);
+    Real fe[9], m7eq, m8eq;
+    f_equilibria<Real>(P, drho, phi, jxe, jye, uxe, uye, dx, dy, lap, fe, m7eq, m8eq);
     // Step 3
     if (MRT) {
         const Real m7 = ((f[1] + f[2]) - (f[3] + f[4])) - m7eq;
@@ -287,6 +311,19 @@ __device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&
         for (int i = 1; i < 9; ++i) fo[i] = fe[i] + k * (f[i] - fe[i]);
     }
     fo[0] = drho - ((((fo[1] + fo[2]) + (fo[3] + fo[4])) + ((fo[5] + fo[6]) + (fo[7] + fo[8]))));
+    uxe_out = uxe;
+    uye_out = uye;
+}
+
+template <typename Real, bool MRT>
+__device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&f)[9],
+                                        const Real (&g)[9], Real phi, Real dx, Real dy, Real lap,
+                                        bool step2, bool step2_relax_j, Real (&fo)[9],
+                                        Real (&go)[9])
+{
+    Real uxe, uye, ge[9];
+    collide_f<Real, MRT>(P, f, phi, dx, dy, lap, step2, step2_relax_j, fo, uxe, uye);
+    g_equilibria<Real>(phi, gamma_mu<Real>(P, phi, lap), uxe, uye, ge);
     // Eq. (gevo); tau_phi = 1 (Sec. III.B) leaves g' = g^eq
     if (P.omega_phi == Real(1)) {
 #pragma unroll

@@ -7,10 +7,30 @@ int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
                     int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
                     void* stream)
 {
+    if (d.compact) {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        return int(coll ? launch_step_compact_w<true>(d, d_descs, d_items, n_items, n_dom, parity,
+                                                      bx, rows, grid_p, sched, s)
+                        : launch_step_compact_w<false>(d, d_descs, d_items, n_items, n_dom,
+                                                       parity, bx, rows, grid_p, sched, s));
+    }
     return launch_step_prec<float>(coll, d, d_descs, d_items, n_items, n_dom, parity, bx, rows,
                                    grid_p, sched, stream);
 }
 
-int prepare_step_f32() { return prepare_step_prec<float>(); }
+int prepare_step_f32()
+{
+    int e = prepare_step_prec<float>();
+    const cudaError_t r[] = {
+        allow_large_smem_compact<false, 0>(), allow_large_smem_compact<false, 2>(),
+        allow_large_smem_compact<false, 4>(), allow_large_smem_compact<false, 8>(),
+        allow_large_smem_compact<true, 0>(),  allow_large_smem_compact<true, 2>(),
+        allow_large_smem_compact<true, 4>(),  allow_large_smem_compact<true, 8>()};
+    for (cudaError_t v : r)
+        if (v != cudaSuccess) e = int(v);
+    return e;
+}
+
+size_t step_smem_bytes_compact(int bx) { return StageLayoutC(bx / 32, kStagesC).total(); }
 
 }  // namespace lbfe

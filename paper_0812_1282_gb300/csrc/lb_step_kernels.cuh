@@ -12,6 +12,7 @@
 
 #include "lb_internal.h"
 #include "lb_step.cuh"
+#include "lb_step_compact.cuh"
 
 namespace lbfe {
 
@@ -91,6 +92,90 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
     }
 }
 
+// Compact-g forms (FP32, tau_phi = 1; lb_step_compact.cuh).  Same launch
+// shapes and scheduling as above.
+template <bool MRT, int NWC>
+__global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int parity, int rows)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int S = kStagesC;
+    const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
+    init_stages<float, S, NWC>(smem, NW);
+    const int warp = int(threadIdx.x >> 5);
+    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
+    unsigned q = 0;
+    if (warp == 0) {
+        produce_tile_c<S, NWC>(D, parity, x0, y0, rows, smem, NW, q);
+        drain_stages<float, S, NWC>(smem, NW, q, D.err);
+    } else {
+        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, smem, NW, warp - 1, q);
+    }
+}
+
+template <bool MRT, int NWC>
+__global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* __restrict__ descs,
+                                                                 const WorkItem* __restrict__ items,
+                                                                 int n_items, int parity,
+                                                                 int* sched, unsigned* err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int tags[kStagesC];
+    constexpr int S = kStagesC;
+    const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
+    init_stages<float, S, NWC>(smem, NW);
+    const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    unsigned q = 0;
+    if (warp == 0) {
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(sched, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n_items) {
+                produce_end<float, S, NWC>(smem, NW, q, tags, err);
+                break;
+            }
+            const WorkItem w = items[it];
+            const DomDesc D = descs[w.dom];
+            produce_tile_c<S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, q, tags, it);
+        }
+        drain_stages<float, S, NWC>(smem, NW, q, err);
+        if (lane == 0) {
+            __threadfence();
+            if (atomicAdd(sched + 1, 1) == int(gridDim.x) - 1) {
+                sched[0] = 0;
+                sched[1] = 0;
+                __threadfence();
+            }
+        }
+    } else {
+        for (;;) {
+            const int it = next_tag<float, S, NWC>(smem, NW, q, tags, err);
+            if (it < 0 || it >= n_items) break;
+            const WorkItem w = items[it];
+            const DomDesc D = descs[w.dom];
+            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
+        }
+    }
+}
+
+template <bool MRT, int NWC>
+cudaError_t launch_step_compact_t(const DomDesc& d, const DomDesc* d_descs,
+                                  const WorkItem* d_items, int n_items, int n_dom, int parity,
+                                  int bx, int rows, int grid_p, int* sched, cudaStream_t s)
+{
+    const size_t smem = StageLayoutC(bx / 32, kStagesC).total();
+    const int threads = bx + 32;
+    if (n_dom == 1 && d_items == nullptr) {
+        dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
+        step_single_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows);
+    } else {
+        const int grid = grid_p > 0 ? grid_p : n_items;
+        step_batch_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d_descs, d_items, n_items,
+                                                                        parity, sched, d.err);
+    }
+    return cudaGetLastError();
+}
+
 template <typename Real, bool MRT, int NWC>
 cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                           int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
@@ -107,6 +192,27 @@ cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkIt
                                                                       parity, sched, d.err);
     }
     return cudaGetLastError();
+}
+
+template <bool MRT>
+cudaError_t launch_step_compact_w(const DomDesc& d, const DomDesc* d_descs,
+                                  const WorkItem* d_items, int n_items, int n_dom, int parity,
+                                  int bx, int rows, int grid_p, int* sched, cudaStream_t s)
+{
+    switch (bx) {
+        case 64:
+            return launch_step_compact_t<MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
+        case 128:
+            return launch_step_compact_t<MRT, 4>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
+        case 256:
+            return launch_step_compact_t<MRT, 8>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
+        default:
+            return launch_step_compact_t<MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
+    }
 }
 
 template <typename Real, bool MRT>
@@ -140,6 +246,18 @@ int launch_step_prec(int coll, const DomDesc& d, const DomDesc* d_descs, const W
                                                 rows, grid_p, sched, s)
                     : launch_step_w<Real, false>(d, d_descs, d_items, n_items, n_dom, parity, bx,
                                                  rows, grid_p, sched, s));
+}
+
+template <bool MRT, int NWC>
+cudaError_t allow_large_smem_compact()
+{
+    const int bytes = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(step_single_compact_kernel<MRT, NWC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_batch_compact_kernel<MRT, NWC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 // Opt every instantiation in to large dynamic shared memory.
