@@ -99,7 +99,8 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
         off = align_up(off + nodes * es, kAlign);
         max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
         max_nx = std::max<long long>(max_nx, nx[d]);
-        item_cap += (long long)((nx[d] + kMinBlockX - 1) / kMinBlockX) * ny[d];
+        // strips are at least 28 columns wide (the compact step's narrowest)
+        item_cap += (long long)((nx[d] + kMinBlockX - 5) / (kMinBlockX - 4)) * ny[d];
         pts_cap = std::max(pts_cap, 16 * (nx[d] + ny[d]));
     }
     L.item_cap = item_cap;
@@ -226,8 +227,10 @@ int build_items(lb_handle* h)
     for (int d : order) {
         const DomDesc& D = h->descs[d];
         if (D.cls) continue;  // stepped by the obstacle kernels
+        // the compact step's strips leave room for four halo columns
+        const int strip = D.compact ? h->block_x - 4 : h->block_x;
         for (int y0 = 0; y0 < D.ny; y0 += h->rows)
-            for (int x0 = 0; x0 < D.nx; x0 += h->block_x)
+            for (int x0 = 0; x0 < D.nx; x0 += strip)
                 items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0)});
     }
     if ((long long)items.size() > h->L.item_cap)

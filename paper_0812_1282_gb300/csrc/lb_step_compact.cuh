@@ -15,19 +15,20 @@
 //               = phi(r, t) + [sum_{i>0} g'_i(r - e_i) - sum_{i>0} g'_i(r)],
 // advanced as an exact integer add of the quantised bracket on the word.
 //
-// Pipeline (as the full-storage step, lb_step.cuh): warp 0 copies, for
-// stage p of a tile, the 9 pulled f segments of row y and the 4 compact
-// segments of row y + 2 (rows above and below the tile get compact-only
-// stages).  Each compute warp
-//   1. expands the compact row it receives into the 8 outgoing g'_i, their
-//      sum and the phi word, for its 32 columns and two halo columns on each
-//      side, into a warp-private 3-row ring;
-//   2. forms phi(t+1) of row y + 1 from that ring (its 32 columns and one
-//      halo column each side, all alike) into its 4-row phi ring;
-//   3. collides row y (f from the stage, the phi stencil from the ring) and
-//      stores 9 f and the node's new compact values.
-// Each stage is consumed within one iteration, so a 3-slot stage ring keeps
-// two rows of copies in flight.
+// Pipeline.  A CTA of NW compute warps owns a strip of W = 32 NW - 4
+// columns, so that each of the three per-row phases below is one pass over
+// its 32 NW compute threads: W + 4 expanded columns, W + 2 phi entries and W
+// nodes.  Warp 0 (the producer) copies, for stage p of a tile, the 9 pulled f
+// segments of row y and the 4 compact segments of row y + 2 (rows above and
+// below the tile get compact-only stages).  The compute threads then, per row,
+//   1. expand the compact row they receive into the 8 outgoing g'_i, their
+//      sum and the phi word, one column each, into a CTA-wide 3-row ring;
+//   2. form phi(t+1) of row y + 1 from that ring, one entry each, into a
+//      CTA-wide 4-row phi ring (and the new words into a 2-row word ring);
+//   3. collide row y (f from the stage, the phi stencil from the ring, the
+//      wall ghost rows mirrored on the fly) and store 9 f and 4 values.
+// Phases 1 -> 2 and 2 -> 3 read what other warps wrote, so the compute warps
+// meet at two mbarriers per row (bounded waits, as every wait here).
 #pragma once
 
 #include "lb_async.cuh"
@@ -38,26 +39,32 @@
 namespace lbfe {
 
 constexpr int kStagesC = 3;    // stage-ring depth of the compact step
-constexpr int kECols = 36;     // expanded columns per warp: 32 + 2 halo each side
 constexpr int kEArrays = 10;   // phi word, g'_1..g'_8, sum of g'_1..g'_8
-constexpr int kESlots = 3;     // expanded rows kept per warp
+constexpr int kESlots = 3;     // expanded rows kept
 
-// Shared memory of one CTA (byte offsets): barriers, S stages of 13
-// segments, then per compute warp the expanded-row ring and the phi ring.
+// Strip width of the compact step for a CTA of bx compute threads.
+__host__ __device__ constexpr int compact_strip(int bx) { return bx - 4; }
+
+// Shared memory of one CTA (byte offsets): stage barriers (full at 0, empty
+// at 64, the two compute-warp barriers at 32 and 40), S stages of 13
+// segments, the expanded-row ring, the phi ring and the word ring.
 struct StageLayoutC {
-    int NW, S, W, segw;
-    __host__ __device__ StageLayoutC(int nw, int s) : NW(nw), S(s), W(32 * nw), segw(32 * nw + 8)
+    int NW, S, W, segw, EC, PC;
+    __host__ __device__ StageLayoutC(int nw, int s)
+        : NW(nw), S(s), W(32 * nw - 4), segw(32 * nw + 4), EC(32 * nw), PC(32 * nw - 2)
     {
     }
     __host__ __device__ size_t full() const { return 0; }
+    __host__ __device__ size_t sync_a() const { return 32; }
+    __host__ __device__ size_t sync_b() const { return 40; }
     __host__ __device__ size_t empty() const { return 64; }
     __host__ __device__ size_t stages() const { return 128; }
     __host__ __device__ size_t stage_elems() const { return size_t(13) * segw; }
     __host__ __device__ size_t erings() const { return stages() + size_t(S) * stage_elems() * 4; }
-    __host__ __device__ size_t ering_elems() const { return size_t(kESlots) * kEArrays * kECols; }
-    __host__ __device__ size_t prings() const { return erings() + size_t(NW) * ering_elems() * 4; }
-    __host__ __device__ size_t wrings() const { return prings() + size_t(NW) * 4 * 34 * 4; }
-    __host__ __device__ size_t total() const { return wrings() + size_t(NW) * 34 * 4; }
+    __host__ __device__ size_t ering_elems() const { return size_t(kESlots) * kEArrays * EC; }
+    __host__ __device__ size_t prings() const { return erings() + ering_elems() * 4; }
+    __host__ __device__ size_t wrings() const { return prings() + size_t(4) * PC * 4; }
+    __host__ __device__ size_t total() const { return wrings() + size_t(2) * PC * 4; }
 };
 
 // Stages of one tile: npro compact-only stages for the compact rows
@@ -80,6 +87,24 @@ struct TilePlanC {
     }
     __device__ __forceinline__ int count() const { return npro + (y1 - y0); }
 };
+
+template <int S>
+__device__ __forceinline__ void init_stages_c(unsigned char* smem, int NW)
+{
+    const StageLayoutC L(NW, S);
+    if (threadIdx.x == 0) {
+        uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
+        uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
+        for (int k = 0; k < S; ++k) {
+            mbar_init(full + k, 1);
+            mbar_init(empty + k, NW);
+        }
+        mbar_init(reinterpret_cast<uint64_t*>(smem + L.sync_a()), NW);
+        mbar_init(reinterpret_cast<uint64_t*>(smem + L.sync_b()), NW);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
 
 // ----------------------------------------------------------- producer
 template <int S, int NWC = 0>
@@ -141,10 +166,13 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
 }
 
 // ----------------------------------------------------------- consumer
+// Compute warp cw of NW; its thread t = 32 cw + lane handles expanded column
+// t, phi entry t and node column t of the strip.  sync_phase carries the
+// parities of the two compute-warp barriers across the tiles of a CTA.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, unsigned char* __restrict__ smem, int nw,
-                                               int cw, unsigned& q)
+                                               int cw, unsigned& q, unsigned& sync_phase)
 {
     const int NW = NWC > 0 ? NWC : nw;
     float* __restrict__ fd = static_cast<float*>(parity ? D.f[0] : D.f[1]);
@@ -154,26 +182,27 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const bool walls = D.walls != 0;
     const NodeParams<float> prm = node_params<float>(D);
     const StageLayoutC L(NW, S);
-    const int segw = L.segw;
+    const int segw = L.segw, EC = L.EC, PC = L.PC;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
+    uint64_t* bar_a = reinterpret_cast<uint64_t*>(smem + L.sync_a());
+    uint64_t* bar_b = reinterpret_cast<uint64_t*>(smem + L.sync_b());
     const float* stage = reinterpret_cast<const float*>(smem + L.stages());
-    float* ering = reinterpret_cast<float*>(smem + L.erings()) + size_t(cw) * L.ering_elems();
-    float* pring = reinterpret_cast<float*>(smem + L.prings()) + cw * 4 * 34;
-    float* wring = reinterpret_cast<float*>(smem + L.wrings()) + cw * 34;  // new words of a row
+    float* ering = reinterpret_cast<float*>(smem + L.erings());
+    float* pring = reinterpret_cast<float*>(smem + L.prings());
+    float* wring = reinterpret_cast<float*>(smem + L.wrings());
 
     const int lane = threadIdx.x & 31;
+    const int t = 32 * cw + lane;
     const TilePlanC T(y0, rows, ny, walls);
     const unsigned qb = q;
     q += unsigned(T.count());
 
-    const int wx0 = x0 + 32 * cw;          // first column of this warp
-    const int wcols = min(32, nx - wx0);   // may be <= 0 for a ragged tile
-    const bool active = lane < wcols;
-    const int ecols = wcols + 4;           // expanded columns: wx0-2 .. wx0+wcols+1
-    const int x = wx0 + lane;
-    const int ci = 32 * cw + lane + 4;     // segment index of the lane's column
-    const int own = lane + 1;              // phi ring entry of the lane's column
+    const int ncols = min(L.W, nx - x0);   // node columns of this strip (>= 1)
+    const bool e_on = t < ncols + 4;       // expanded column t: lattice x0 - 2 + t
+    const bool p_on = t < ncols + 2;       // phi entry t: lattice x0 - 1 + t
+    const bool n_on = t < ncols;           // node column t: lattice x0 + t
+    const int x = x0 + t;
 
     auto slot_of = [&](int p) { return (qb + unsigned(p)) % unsigned(S); };
     auto stage_ptr = [&](int p) { return stage + size_t(slot_of(p)) * L.stage_elems(); };
@@ -185,139 +214,144 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + slot_of(p));
     };
-    auto eslot = [&](int yl) -> float* {
-        return ering + ((yl - y0 + 2) % kESlots) * (kEArrays * kECols);
+    // all compute warps meet at barrier a (bit 0 of sync_phase) or b (bit 1):
+    // writes before the meeting are visible to reads after it
+    auto meet = [&](uint64_t* bar, unsigned bit) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar);
+        mbar_wait(bar, (sync_phase & bit) ? 1u : 0u, D.err);
+        sync_phase ^= bit;
     };
-    auto rslot = [&](int y) -> float* { return pring + ((y - y0 + 1) & 3) * 34; };
+    auto eslot = [&](int yl) -> float* {
+        return ering + ((yl - y0 + 2) % kESlots) * (kEArrays * EC);
+    };
+    auto rslot = [&](int y) -> float* { return pring + ((y - y0 + 1) & 3) * PC; };
+    auto wslot = [&](int y) -> float* { return wring + (y & 1) * PC; };
 
-    // 1. expand compact row yl (stage p): column j of the ring is lattice
-    //    column wx0 - 2 + j, segment index 32 cw + j + 2
+    // 1. expand compact row yl (stage p): column t, segment index t + 2
     auto expand = [&](int p, int yl) {
+        if (!e_on) return;
         const float* sc = stage_ptr(p) + 9 * segw;
         float* e = eslot(yl);
-        for (int j = lane; j < ecols; j += 32) {
-            const int si = 32 * cw + j + 2;
-            const float word = sc[si];
-            const float phi = G0<float>::value(word);
-            float ge[9];
-            g_equilibria<float>(phi, sc[segw + si], sc[2 * segw + si], sc[3 * segw + si], ge);
-            e[j] = word;
+        const int si = t + 2;
+        const float word = sc[si];
+        const float phi = G0<float>::value(word);
+        float ge[9];
+        g_equilibria<float>(phi, sc[segw + si], sc[2 * segw + si], sc[3 * segw + si], ge);
+        e[t] = word;
 #pragma unroll
-            for (int a = 1; a < 9; ++a) e[a * kECols + j] = ge[a];
-            e[9 * kECols + j] = g_tail_sum<float>(ge);
-        }
+        for (int a = 1; a < 9; ++a) e[a * EC + t] = ge[a];
+        e[9 * EC + t] = g_tail_sum<float>(ge);
     };
-    // 2. phi(t+1) of real row r at ring column j; returns the new word
-    auto phi_next = [&](int r, int j, float& phi_out) -> float {
+    // 2. phi(t+1) of real row r at entry t (expanded column j = t + 1)
+    auto publish = [&](int r) {
+        if (!p_on) return;
+        const int j = t + 1;
         const bool blo = walls && r == 0, bhi = walls && r == ny - 1;
         const float* m = eslot(r);
         const float* b = blo ? m : eslot(r - 1);
         const float* a = bhi ? m : eslot(r + 1);
-        const float g1 = m[1 * kECols + j - 1];
-        const float g2 = m[2 * kECols + j + 1];
-        const float g3 = blo ? m[4 * kECols + j] : b[3 * kECols + j];
-        const float g4 = bhi ? m[3 * kECols + j] : a[4 * kECols + j];
-        const float g5 = blo ? m[6 * kECols + j] : b[5 * kECols + j - 1];
-        const float g6 = bhi ? m[5 * kECols + j] : a[6 * kECols + j + 1];
-        const float g7 = blo ? m[8 * kECols + j] : b[7 * kECols + j + 1];
-        const float g8 = bhi ? m[7 * kECols + j] : a[8 * kECols + j - 1];
+        const float g1 = m[1 * EC + j - 1];
+        const float g2 = m[2 * EC + j + 1];
+        const float g3 = blo ? m[4 * EC + j] : b[3 * EC + j];
+        const float g4 = bhi ? m[3 * EC + j] : a[4 * EC + j];
+        const float g5 = blo ? m[6 * EC + j] : b[5 * EC + j - 1];
+        const float g6 = bhi ? m[5 * EC + j] : a[6 * EC + j + 1];
+        const float g7 = blo ? m[8 * EC + j] : b[7 * EC + j + 1];
+        const float g8 = bhi ? m[7 * EC + j] : a[8 * EC + j - 1];
         const float tail_in = (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
-        const float word = G0<float>::advance(m[j], tail_in - m[9 * kECols + j]);
-        phi_out = G0<float>::value(word);
-        return word;
-    };
-    // publish row r (real): phi(t+1) at the ring entries k = 0 .. wcols + 1
-    // (lattice columns wx0 - 1 .. wx0 + wcols, expanded column j = k + 1),
-    // every entry computed alike; the new words go to the word ring, from
-    // which each lane takes its own (entry lane + 1) after a __syncwarp
-    auto publish = [&](int r) {
-        float* s = rslot(r);
-        for (int k = lane; k < wcols + 2; k += 32) {
-            float ph;
-            wring[k] = phi_next(r, k + 1, ph);
-            s[k] = ph;
-        }
-    };
-    auto ghost_row = [&](int yg, int ys, float h2) {
-        float* sg = rslot(yg);
-        const float* ss = rslot(ys);
-        for (int k = lane; k < wcols + 2; k += 32) sg[k] = ss[k] - h2;
+        const float word = G0<float>::advance(m[j], tail_in - m[9 * EC + j]);
+        rslot(r)[t] = G0<float>::value(word);
+        wslot(r)[t] = word;
     };
     // compact rows up to e expanded: is row r ready to publish?
     auto ready = [&](int r, int e) { return e >= min(r + 1, T.chi); };
 
     const int y1 = T.y1;
-    const bool bottom_ghost = walls && y0 == 0;
-    int pub = bottom_ghost ? 0 : y0 - 1;
-    float wcur = 0.f, wnext = 0.f;
+    int pub = (walls && y0 == 0) ? 0 : y0 - 1;
     int p = 0;
     // prologue: compact-only stages; publish rows y0-1 (unless a wall ghost) and y0
     for (; p < T.npro; ++p) {
         const int yl = T.clo + p;
         wait_full(p);
-        if (wcols > 0) expand(p, yl);
-        release(p);  // includes __syncwarp: the expanded row is visible to the warp
+        expand(p, yl);
+        release(p);
+        meet(bar_a, 1u);
+        bool any = false;
         while (pub <= y0 && ready(pub, yl)) {
-            if (wcols > 0) publish(pub);
-            __syncwarp();
-            if (pub == y0 && active) wcur = wring[own];
+            publish(pub);
             ++pub;
+            any = true;
         }
-        __syncwarp();  // publish reads the ring rows the next expansion overwrites
+        if (any) meet(bar_b, 2u);
     }
+    const float h2b = 2.f * prm.h_bot, h2t = 2.f * prm.h_top;
     for (int y = y0; y < y1; ++y, ++p) {
         wait_full(p);
-        if (wcols > 0 && y + 2 <= T.chi) expand(p, y + 2);
-        __syncwarp();
+        if (y + 2 <= T.chi) expand(p, y + 2);
+        meet(bar_a, 1u);
         const int yn = y + 1;
-        if (walls && yn == ny) {
-            ghost_row(ny, ny - 2, 2.f * prm.h_top);
-        } else if (wcols > 0) {
-            publish(yn);
-        }
-        __syncwarp();
-        if (!(walls && yn == ny) && active) wnext = wring[own];
-        if (bottom_ghost && y == 0) ghost_row(-1, 1, 2.f * prm.h_bot);
-        __syncwarp();
-        if (active) {
+        if (!(walls && yn == ny)) publish(yn);
+        meet(bar_b, 2u);
+        if (n_on) {
             const bool blo = walls && y == 0, bhi = walls && y == ny - 1;
             const float* sb = stage_ptr(p);
             float f[9];
-            read9<float>(sb, segw, ci, blo, bhi, f);
-            const float* sm = rslot(y - 1);
+            read9<float>(sb, segw, t + 4, blo, bhi, f);
+            const int k = t + 1;  // phi entry of the node
             const float* sc = rslot(y);
-            const float* sp = rslot(y + 1);
-            const float c = sc[own];
+            const float c = sc[k], e = sc[k + 1], w = sc[k - 1];
+            float n, ne, nw, s, se, sw;
+            if (bhi) {  // ghost row ny: mirror of row ny - 2
+                const float* sq = rslot(ny - 2);
+                n = sq[k] - h2t;
+                ne = sq[k + 1] - h2t;
+                nw = sq[k - 1] - h2t;
+            } else {
+                const float* sp = rslot(y + 1);
+                n = sp[k];
+                ne = sp[k + 1];
+                nw = sp[k - 1];
+            }
+            if (blo) {  // ghost row -1: mirror of row 1
+                const float* sq = rslot(1);
+                s = sq[k] - h2b;
+                se = sq[k + 1] - h2b;
+                sw = sq[k - 1] - h2b;
+            } else {
+                const float* sm = rslot(y - 1);
+                s = sm[k];
+                se = sm[k + 1];
+                sw = sm[k - 1];
+            }
             float dx, dy, lap;
-            stencils<float>(c, sc[own + 1], sc[own - 1], sp[own], sm[own], sp[own + 1],
-                            sp[own - 1], sm[own + 1], sm[own - 1], dx, dy, lap);
+            stencils<float>(c, e, w, n, s, ne, nw, se, sw, dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
             float fo[9], uxe, uye;
             collide_f<float, MRT>(prm, f, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, uxe, uye);
             const float G = gamma_mu<float>(prm, c, lap);
             const int o = y * pitch + x + kXOff;
-            const float co[4] = {wcur, G, uxe, uye};
+            const float co[4] = {wslot(y)[k], G, uxe, uye};
 #pragma unroll
             for (int i = 0; i < 9; ++i) fd[i * P + o] = fo[i];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) cd[k * P + o] = co[k];
+            for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co[kk];
             // periodic ghost copies: logical 0, 1 also at nx, nx+1 and
             // logical nx-2, nx-1 also at -2, -1
             if (x < 2) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) fd[i * P + o + nx] = fo[i];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) cd[k * P + o + nx] = co[k];
+                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + nx] = co[kk];
             }
             if (x >= nx - 2) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) fd[i * P + o - nx] = fo[i];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) cd[k * P + o - nx] = co[k];
+                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o - nx] = co[kk];
             }
         }
         release(p);
-        wcur = wnext;
     }
 }
 

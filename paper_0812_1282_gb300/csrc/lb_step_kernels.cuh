@@ -93,22 +93,22 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
 }
 
 // Compact-g forms (FP32, tau_phi = 1; lb_step_compact.cuh).  Same launch
-// shapes and scheduling as above.
+// shapes and scheduling as above, with strips of compact_strip(bx) columns.
 template <bool MRT, int NWC>
 __global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int parity, int rows)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStagesC;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
-    init_stages<float, S, NWC>(smem, NW);
+    init_stages_c<S>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
-    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
-    unsigned q = 0;
+    const int x0 = blockIdx.x * compact_strip(32 * NW), y0 = blockIdx.y * rows;
+    unsigned q = 0, sync_phase = 0;
     if (warp == 0) {
         produce_tile_c<S, NWC>(D, parity, x0, y0, rows, smem, NW, q);
         drain_stages<float, S, NWC>(smem, NW, q, D.err);
     } else {
-        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, smem, NW, warp - 1, q);
+        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, smem, NW, warp - 1, q, sync_phase);
     }
 }
 
@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
     __shared__ int tags[kStagesC];
     constexpr int S = kStagesC;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
-    init_stages<float, S, NWC>(smem, NW);
+    init_stages_c<S>(smem, NW);
     const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
-    unsigned q = 0;
+    unsigned q = 0, sync_phase = 0;
     if (warp == 0) {
         for (;;) {
             int it = 0;
@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
             if (it < 0 || it >= n_items) break;
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
-            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
+            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q,
+                                        sync_phase);
         }
     }
 }
@@ -166,7 +167,8 @@ cudaError_t launch_step_compact_t(const DomDesc& d, const DomDesc* d_descs,
     const size_t smem = StageLayoutC(bx / 32, kStagesC).total();
     const int threads = bx + 32;
     if (n_dom == 1 && d_items == nullptr) {
-        dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
+        const int w = compact_strip(bx);
+        dim3 grid((d.nx + w - 1) / w, (d.ny + rows - 1) / rows);
         step_single_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows);
     } else {
         const int grid = grid_p > 0 ? grid_p : n_items;
