@@ -43,7 +43,7 @@ import lbinputs  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
-BYTES_PER_NODE = {"fp32": 144, "fp64": 288}
+BYTES_PER_NODE = {"fp32": 144, "fp64": 288, "fp32c": 104}  # fp32c: compact g storage
 
 
 def kernel_source_hash() -> str:
@@ -210,7 +210,7 @@ def run_headline(lbf, torch, ws, steps, warmup, precision="fp32", size=None, til
                      mass=st["mass"], max_u=st["max_u"], nonfinite=st["nonfinite"])
 
 
-def run_e2e(lbf, torch, steps):
+def run_e2e(lbf, torch, steps, compact=False):
     """The same job through the public API with host buffers: upload phi0
     from pinned host memory, run `steps` steps reading the diagnostics back
     every 100 steps, and download the final phi field."""
@@ -220,7 +220,7 @@ def run_e2e(lbf, torch, steps):
     nx, ny = c["nx"], c["ny"]
     phi0 = torch.from_numpy(lbinputs.random_field(nx, ny, c["amp"], c["seed"])).pin_memory()
     out_phi = torch.empty((ny, nx), dtype=torch.float64).pin_memory()
-    p = lbf.params(precision="fp32", **c["params"])
+    p = lbf.params(precision="fp32", compact_g=compact, **c["params"])
     sim = lbf.Lattice(p, nx, ny)
     sim.autotune(reps=2)
     torch.cuda.synchronize()
@@ -311,7 +311,7 @@ def run_capillary(lbf, torch, steps=None):
                      "half, theory gamma w cos(theta_a) / 6")
 
 
-def run_batched(lbf, torch, steps):
+def run_batched(lbf, torch, steps, compact=False):
     """256 sessile drops (sides 64..512) in one launch per step, against the
     same domains stepped one after another (one launch per domain per step)."""
     specs = lbinputs.batch_specs()
@@ -322,7 +322,7 @@ def run_batched(lbf, torch, steps):
         # the 10000-step job; the throughput is the same either way
         plist.append(lbf.params(collision="mrt", precision="fp32", tau_alpha=s["tau_alpha"],
                                 tau_beta=s["tau_beta"], h_bottom=lbf.lb_wetting_h(s["theta"]),
-                                step2_relax_momentum=True))
+                                step2_relax_momentum=True, compact_g=compact))
         nxs.append(s["nx"])
         nys.append(s["ny"])
     nodes = sum(a * b for a, b in zip(nxs, nys))
@@ -368,7 +368,7 @@ def run_batched(lbf, torch, steps):
                 loop_sims_per_s=len(specs) / (dt_l / steps * full),
                 loop_graph_sims_per_s=len(specs) / (dt_g / steps * full),
                 speedup_vs_loop=dt_l / dt_b, speedup_vs_loop_graph=dt_g / dt_b,
-                tile=list(tile[:2]),
+                tile=list(tile[:2]), storage="compact g" if compact else "full",
                 note="sims/s of the 10000-step job, from %d timed steps; loop = one launch "
                      "per domain per step; loop_graph = each domain's steps replayed from "
                      "its own CUDA graphs, domains in sequence; MRT with the momentum-"
@@ -423,7 +423,7 @@ def ours(args):
     if args.only:
         # one extra workload alone (profiling aid): its JSON object only
         if args.only == "batched":
-            res = run_batched(lbf, torch, max(4, args.steps))
+            res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact")
         else:
             res = run_capillary(lbf, torch, max(1000, args.steps))
         print(json.dumps({"workload": args.only, **res}), flush=True)
@@ -436,11 +436,14 @@ def ours(args):
     sim.close()
     torch.cuda.empty_cache()
     side = args.size or 8192
+    compact = args.storage == "compact"
+    bpn = BYTES_PER_NODE["fp32c" if compact else "fp32"]
     dt = max_over_ranks(ws, head["seconds"])
     value = job_value(head["nodes"], args.steps, ws, dt)
     per_launch = dt / args.steps
-    achieved = head["nodes"] * BYTES_PER_NODE["fp32"] / per_launch / 1e9
-    traffic = profile_traffic("lb_step_mrt_fp32_8192") if side == 8192 else None
+    achieved = head["nodes"] * bpn / per_launch / 1e9
+    prof = "lb_step_compact_mrt_fp32_8192" if compact else "lb_step_mrt_fp32_8192"
+    traffic = profile_traffic(prof) if side == 8192 else None
     line = {
         "metric": "MLUPS (MRT, FP32, 8192^2) and HBM-roofline fraction",
         "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -450,19 +453,22 @@ def ours(args):
         "config": {"workload": "spinodal %dx%d D2Q9 two-population MRT (FP32 deviation "
                                "storage), walls y=0/%d, seed 12345" % (side, side, side - 1),
                    "nx": side, "ny": side, "collision": "mrt", "tile": head["tile"],
+                   "storage": ("compact g: phi word, Gamma mu, u_eq per node (tau_phi = 1); "
+                               "9 f + 4 values = 104 B per node update") if compact else
+                              "full: 9 f + 9 g = 144 B per node update",
                    "l2": "state %.1f GB >> 129 MB L2, no flush needed"
-                         % (side * side * BYTES_PER_NODE["fp32"] / 1e9),
+                         % (side * side * bpn / 1e9),
                    "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "traffic": traffic,
                      "peak_source": "%s MEASURED_PEAKS.json hbm_gbs" % peak_kind,
-                     "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"]},
+                     "algorithmic_bytes_per_node": bpn},
         "gpu_launches": head["launches"],
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.quick:
-        e2e = run_e2e(lbf, torch, args.steps)
+        e2e = run_e2e(lbf, torch, args.steps, compact=compact)
         line["e2e"] = {"value": round(head["nodes"] * args.steps / e2e["seconds"] / 1e6, 1),
                        "unit": "MLUPS", "h2d_bytes_per_step": e2e["h2d"] // args.steps,
                        "d2h_bytes_per_step": e2e["d2h"] // args.steps,
@@ -470,6 +476,21 @@ def ours(args):
                               "steps, final phi D2H" % args.steps}
         torch.cuda.empty_cache()
         extras = {}
+        if compact:
+            # the same workload with full g storage (144 B per node update)
+            try:
+                simf, headf = run_headline(lbf, torch, 1, max(20, args.steps // 2), args.warmup,
+                                           size=args.size, compact=False)
+                simf.close()
+                nf = headf["nodes"] * max(20, args.steps // 2)
+                gbs = nf * BYTES_PER_NODE["fp32"] / headf["seconds"] / 1e9
+                extras["full_storage"] = {
+                    "mlups": round(nf / headf["seconds"] / 1e6, 1), "tile": headf["tile"],
+                    "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                    "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"]}
+            except Exception as exc:
+                extras["full_storage"] = {"error": str(exc)}
+            torch.cuda.empty_cache()
         try:
             fp64 = run_fp64(lbf, torch, max(4, args.steps // 20))
             fp64["bound"] = "alu"
@@ -479,7 +500,7 @@ def ours(args):
             extras["fp64"] = {"error": str(exc)}
         torch.cuda.empty_cache()
         try:
-            extras["batched"] = run_batched(lbf, torch, max(20, args.steps // 2))
+            extras["batched"] = run_batched(lbf, torch, max(20, args.steps // 2), compact=compact)
         except Exception as exc:
             extras["batched"] = {"error": str(exc)}
         torch.cuda.empty_cache()
@@ -591,7 +612,7 @@ def main():
                     help="side of a smaller square lattice (profiling aid; default 8192)")
     ap.add_argument("--tile", default=None,
                     help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
-    ap.add_argument("--storage", choices=("full", "compact"), default="full",
+    ap.add_argument("--storage", choices=("full", "compact"), default="compact",
                     help="g storage of the headline lattice (compact: phi, Gamma mu, u_eq)")
     ap.add_argument("--only", choices=("batched", "capillary"), default=None,
                     help="run one extra workload alone for --steps steps (profiling aid)")
