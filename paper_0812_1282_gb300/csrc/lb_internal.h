@@ -103,7 +103,6 @@ int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
                     void* stream);
 int prepare_step_f32();
 int prepare_step_f64();
-size_t step_smem_bytes_compact(int bx);
 
 // Dynamic shared memory of the step kernel for a block width (0 if the
 // width is not supported for this precision).

@@ -31,6 +31,4 @@ int prepare_step_f32()
     return e;
 }
 
-size_t step_smem_bytes_compact(int bx) { return StageLayoutC(bx / 32, kStagesC).total(); }
-
 }  // namespace lbfe
