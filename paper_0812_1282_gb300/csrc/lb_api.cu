@@ -227,11 +227,23 @@ int build_items(lb_handle* h)
     for (int d : order) {
         const DomDesc& D = h->descs[d];
         if (D.cls) continue;  // stepped by the obstacle kernels
-        // the compact step's strips leave room for four halo columns
-        const int strip = D.compact ? h->block_x - 4 : h->block_x;
+        if (D.compact) {
+            // the compact step's strips leave room for four halo columns; a
+            // domain is cut into near-equal strips (multiples of 4 columns,
+            // so every bulk copy stays 16-byte aligned) instead of full
+            // strips and one narrow remainder
+            const int wmax = h->block_x - 4;
+            const int k = (D.nx + wmax - 1) / wmax;
+            const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
+            for (int y0 = 0; y0 < D.ny; y0 += h->rows)
+                for (int x0 = 0; x0 < D.nx; x0 += w)
+                    items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0),
+                                             std::min(w, D.nx - x0)});
+            continue;
+        }
         for (int y0 = 0; y0 < D.ny; y0 += h->rows)
-            for (int x0 = 0; x0 < D.nx; x0 += strip)
-                items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0)});
+            for (int x0 = 0; x0 < D.nx; x0 += h->block_x)
+                items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0), 0});
     }
     if ((long long)items.size() > h->L.item_cap)
         return fail(LB_ERR_INVALID_ARG, "work list exceeds its capacity");

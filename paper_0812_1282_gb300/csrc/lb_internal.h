@@ -50,9 +50,10 @@ struct DomDesc {
 constexpr int kMaxClass = 7;
 
 // A rectangular piece of one domain processed by one CTA: columns
-// [x0, x0 + blockDim.x) and rows [y0, y0 + rows).
+// [x0, x0 + cols) and rows [y0, y0 + rows).  cols = 0 means the kernel's
+// full strip width (clipped to the domain).
 struct WorkItem {
-    int dom, x0, y0, rows;
+    int dom, x0, y0, rows, cols;
 };
 
 // Per-domain reduction result written by the moments kernels.

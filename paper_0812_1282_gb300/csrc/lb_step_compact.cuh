@@ -109,8 +109,8 @@ __device__ __forceinline__ void init_stages_c(unsigned char* smem, int NW)
 // ----------------------------------------------------------- producer
 template <int S, int NWC = 0>
 __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int x0, int y0,
-                                               int rows, unsigned char* __restrict__ smem, int nw,
-                                               unsigned& q, int* tags = nullptr, int tag = 0)
+                                               int rows, int cols, unsigned char* __restrict__ smem,
+                                               int nw, unsigned& q, int* tags = nullptr, int tag = 0)
 {
     const int NW = NWC > 0 ? NWC : nw;
     const float* __restrict__ fs = static_cast<const float*>(parity ? D.f[1] : D.f[0]);
@@ -125,7 +125,10 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
     const int lane = threadIdx.x & 31;
     const TilePlanC T(y0, rows, ny, walls);
     const int segw = L.segw;
-    const int seglen = min(segw, pitch - x0);
+    // columns x0-4 .. x0+ncols+3 (ncols rounded up to 4 keeps the copy a
+    // multiple of 16 bytes), within the row's pitch
+    const int ncols = cols > 0 ? cols : min(L.W, D.nx - x0);
+    const int seglen = min(min(segw, (ncols + 3) / 4 * 4 + 8), pitch - x0);
     const uint32_t segbytes = uint32_t(seglen) * 4u;
     const int i = lane % 9;
     const int ey = ey_of(i);
@@ -171,8 +174,8 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
 // parities of the two compute-warp barriers across the tiles of a CTA.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
-                                               int rows, unsigned char* __restrict__ smem, int nw,
-                                               int cw, unsigned& q, unsigned& sync_phase)
+                                               int rows, int cols, unsigned char* __restrict__ smem,
+                                               int nw, int cw, unsigned& q, unsigned& sync_phase)
 {
     const int NW = NWC > 0 ? NWC : nw;
     float* __restrict__ fd = static_cast<float*>(parity ? D.f[0] : D.f[1]);
@@ -198,7 +201,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const unsigned qb = q;
     q += unsigned(T.count());
 
-    const int ncols = min(L.W, nx - x0);   // node columns of this strip (>= 1)
+    const int ncols = cols > 0 ? cols : min(L.W, nx - x0);  // node columns of this strip
     const bool e_on = t < ncols + 4;       // expanded column t: lattice x0 - 2 + t
     const bool p_on = t < ncols + 2;       // phi entry t: lattice x0 - 1 + t
     const bool n_on = t < ncols;           // node column t: lattice x0 + t

@@ -105,10 +105,11 @@ __global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int
     const int x0 = blockIdx.x * compact_strip(32 * NW), y0 = blockIdx.y * rows;
     unsigned q = 0, sync_phase = 0;
     if (warp == 0) {
-        produce_tile_c<S, NWC>(D, parity, x0, y0, rows, smem, NW, q);
+        produce_tile_c<S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, q);
         drain_stages<float, S, NWC>(smem, NW, q, D.err);
     } else {
-        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, smem, NW, warp - 1, q, sync_phase);
+        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, warp - 1, q,
+                                    sync_phase);
     }
 }
 
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
             }
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
-            produce_tile_c<S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, q, tags, it);
+            produce_tile_c<S, NWC>(D, parity, w.x0, w.y0, w.rows, w.cols, smem, NW, q, tags, it);
         }
         drain_stages<float, S, NWC>(smem, NW, q, err);
         if (lane == 0) {
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
             if (it < 0 || it >= n_items) break;
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
-            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q,
-                                        sync_phase);
+            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, w.cols, smem, NW,
+                                        warp - 1, q, sync_phase);
         }
     }
 }
