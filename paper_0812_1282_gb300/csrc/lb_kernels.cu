@@ -176,18 +176,41 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
                 v[r][c] = val;
             }
         }
-        double dx, dy, lap;
-        stencils<double>(v[1][1], v[1][2], v[1][0], v[2][1], v[0][1], v[2][2], v[2][0], v[0][2],
-                         v[0][0], dx, dy, lap);
-        double fe[9], ge[9], m7eq, m8eq;
         const double phi = v[1][1];
-        equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge, m7eq, m8eq);
-        fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
-        ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
+        double fe[9], ge[9], G;
+        if constexpr (sizeof(Real) == 4) {
+            // FP32 storage: the stencils and equilibria in FP32 (the result is
+            // rounded to FP32 anyway; this GPU's FP64 pipe is 1/64 of the FP32
+            // rate), phi and g_0 from the FP64 input
+            const NodeParams<float> pf = node_params<float>(D);
+            float vf[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) vf[r][c] = float(v[r][c]);
+            float dxf, dyf, lapf, fef[9], gef[9], m7f, m8f;
+            stencils<float>(vf[1][1], vf[1][2], vf[1][0], vf[2][1], vf[0][1], vf[2][2], vf[2][0],
+                            vf[0][2], vf[0][0], dxf, dyf, lapf);
+            equilibria<float>(pf, 0.f, vf[1][1], 0.f, 0.f, 0.f, 0.f, dxf, dyf, lapf, fef, gef, m7f,
+                              m8f);
+            fef[0] = -((((fef[1] + fef[2]) + (fef[3] + fef[4])) + ((fef[5] + fef[6]) + (fef[7] + fef[8]))));
+            for (int i = 0; i < 9; ++i) {
+                fe[i] = fef[i];
+                ge[i] = gef[i];
+            }
+            ge[0] = phi - double(g_tail_sum<float>(gef));
+            G = gamma_mu<float>(pf, vf[1][1], lapf);
+        } else {
+            double dx, dy, lap, m7eq, m8eq;
+            stencils<double>(v[1][1], v[1][2], v[1][0], v[2][1], v[0][1], v[2][2], v[2][0], v[0][2],
+                             v[0][0], dx, dy, lap);
+            equilibria<double>(prm, 0.0, phi, 0.0, 0.0, 0.0, 0.0, dx, dy, lap, fe, ge, m7eq, m8eq);
+            fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
+            ge[0] = phi - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
+            G = gamma_mu<double>(prm, phi, lap);
+        }
         const long long o = (long long)y * pitch + x + kXOff;
         const long long og1 = x < 2 ? o + nx : -1, og2 = x >= nx - 2 ? o - nx : -1;
         // compact g storage: (phi word, Gamma mu, u_eq = 0) in planes 0..3
-        const double cg[4] = {0.0, gamma_mu<double>(prm, phi, lap), 0.0, 0.0};
+        const double cg[4] = {0.0, G, 0.0, 0.0};
         for (int i = 0; i < 9; ++i) {
             const Real fv = Real(fe[i]);
             Real gv;
@@ -228,7 +251,7 @@ int launch_init_eq(int precision, const DomDesc& d, const double* phi0, int pari
 // one partial per block, then a single-block pass in fixed order, so the
 // result is deterministic.
 constexpr int kMomBlock = 256;
-constexpr int kMaxMomBlocks = 1024;
+constexpr int kMaxMomBlocks = 4096;  // ~27 blocks of 256 per SM: enough loads in flight
 
 int max_partials_needed(int, int) { return kMaxMomBlocks; }
 
@@ -256,41 +279,98 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(DomDesc D, int parit
     const int nx = D.nx, pitch = D.pitch;
     const long long n = (long long)nx * nrows;
     double acc[kStatsFields] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int yr = int(k / nx), x = int(k - (long long)yr * nx);
-        const long long q = (long long)yr * ld + x;
-        if (D.cls && D.cls[(long long)(row0 + yr) * nx + x] != 0) {
-            // solid node: no fluid, no contribution to the diagnostics
-            if (rho) rho[q] = 0.0;
-            if (phi) phi[q] = 0.0;
-            if (ux) ux[q] = 0.0;
-            if (uy) uy[q] = 0.0;
-            continue;
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 storage: per-node arithmetic in FP32 and per-thread sums of the
+        // small quantities (rho - 1, rho u, the g tail) in FP32, of the phi
+        // words as exact 64-bit integers; widened once per thread (this GPU's
+        // FP64 pipe runs at 1/64 of the FP32 rate)
+        float s_drho = 0.f, s_jx = 0.f, s_jy = 0.f, s_tail = 0.f, s_um = 0.f;
+        long long s_word = 0, s_n = 0;
+        int s_bad = 0;
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+             k += (long long)gridDim.x * blockDim.x) {
+            const int yr = int(k / nx), x = int(k - (long long)yr * nx);
+            const long long q = (long long)yr * ld + x;
+            if (D.cls && D.cls[(long long)(row0 + yr) * nx + x] != 0) {
+                // solid node: no fluid, no contribution to the diagnostics
+                if (rho) rho[q] = 0.0;
+                if (phi) phi[q] = 0.0;
+                if (ux) ux[q] = 0.0;
+                if (uy) uy[q] = 0.0;
+                continue;
+            }
+            const long long o = (long long)(row0 + yr) * pitch + x + kXOff;
+            float f[9];
+            for (int i = 0; i < 9; ++i) f[i] = float(fs[i * P + o]);
+            const float drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+            const float jxf = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const float jyf = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
+            float tail = 0.f;
+            if (!D.compact) {
+                float g[9];
+                for (int i = 1; i < 9; ++i) g[i] = float(gs[i * P + o]);
+                tail = g_tail_sum<float>(g);
+            }
+            const float word_raw = float(gs[o]);
+            const float rf = 1.f + drho;
+            const float vxf = jxf / rf, vyf = jyf / rf;
+            const float umf = sqrtf(vxf * vxf + vyf * vyf);
+            if (rho) rho[q] = 1.0 + double(drho);
+            if (phi) phi[q] = G0<float>::decode(word_raw) + double(tail);
+            if (ux) ux[q] = double(vxf);
+            if (uy) uy[q] = double(vyf);
+            const bool finite = isfinite(drho) && isfinite(tail) && isfinite(umf);
+            s_drho += drho;
+            s_jx += jxf;
+            s_jy += jyf;
+            s_tail += tail;
+            s_word += __float_as_int(word_raw);
+            ++s_n;
+            s_um = finite ? fmaxf(s_um, umf) : s_um;
+            s_bad += finite ? 0 : 1;
         }
-        const long long o = (long long)(row0 + yr) * pitch + x + kXOff;
-        double f[9], g[9];
-        for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
-        g[0] = G0<Real>::decode(gs[o]);
-        for (int i = 1; i < 9; ++i) g[i] = D.compact ? 0.0 : double(gs[i * P + o]);
-        const double drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
-        const double jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const double jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
-        const double ph = phi_sum<double>(g);
-        const double r = 1.0 + drho;
-        const double vx = jx / r, vy = jy / r;
-        if (rho) rho[q] = r;
-        if (phi) phi[q] = ph;
-        if (ux) ux[q] = vx;
-        if (uy) uy[q] = vy;
-        const double um = sqrt(vx * vx + vy * vy);
-        const bool finite = isfinite(r) && isfinite(ph) && isfinite(um);
-        acc[0] += r;
-        acc[1] += ph;
-        acc[2] += jx;
-        acc[3] += jy;
-        acc[4] = finite ? fmax(acc[4], um) : acc[4];
-        acc[5] += finite ? 0.0 : 1.0;
+        acc[0] = double(s_n) + double(s_drho);
+        acc[1] = double(s_word) / G0<float>::kScale + double(s_tail);
+        acc[2] = double(s_jx);
+        acc[3] = double(s_jy);
+        acc[4] = double(s_um);
+        acc[5] = double(s_bad);
+    } else {
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+             k += (long long)gridDim.x * blockDim.x) {
+            const int yr = int(k / nx), x = int(k - (long long)yr * nx);
+            const long long q = (long long)yr * ld + x;
+            if (D.cls && D.cls[(long long)(row0 + yr) * nx + x] != 0) {
+                if (rho) rho[q] = 0.0;
+                if (phi) phi[q] = 0.0;
+                if (ux) ux[q] = 0.0;
+                if (uy) uy[q] = 0.0;
+                continue;
+            }
+            const long long o = (long long)(row0 + yr) * pitch + x + kXOff;
+            double f[9], g[9];
+            for (int i = 0; i < 9; ++i) f[i] = double(fs[i * P + o]);
+            g[0] = G0<Real>::decode(gs[o]);
+            for (int i = 1; i < 9; ++i) g[i] = D.compact ? 0.0 : double(gs[i * P + o]);
+            const double drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+            const double jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const double jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[7] - f[8]);
+            const double ph = phi_sum<double>(g);
+            const double r = 1.0 + drho;
+            const double vx = jx / r, vy = jy / r;
+            if (rho) rho[q] = r;
+            if (phi) phi[q] = ph;
+            if (ux) ux[q] = vx;
+            if (uy) uy[q] = vy;
+            const double um = sqrt(vx * vx + vy * vy);
+            const bool finite = isfinite(r) && isfinite(ph) && isfinite(um);
+            acc[0] += r;
+            acc[1] += ph;
+            acc[2] += jx;
+            acc[3] += jy;
+            acc[4] = finite ? fmax(acc[4], um) : acc[4];
+            acc[5] += finite ? 0.0 : 1.0;
+        }
     }
     if (partials == nullptr) return;
     warp_reduce(acc);
