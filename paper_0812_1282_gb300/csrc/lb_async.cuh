@@ -94,25 +94,87 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 // Wait for the phase of `bar` with the given parity; bounded.  Gives up
-// after kWaitNs of wall time, or at once when another waiter already
-// recorded a failure, so a lost completion costs at most one timeout per
-// waiter rather than a hang.  Returns false (and sets bit kErrTimeout of
-// *err) when it gives up.
+// after kWaitNs of wall time, or when another waiter already recorded a
+// failure, so a lost completion costs at most one timeout per waiter rather
+// than a hang.  Returns false (and sets bit kErrTimeout of *err) when it
+// gives up.
+//
+// The polls themselves suspend in hardware until the phase completes or a
+// short time passes.  The clock and the error word (a global load, about a
+// microsecond) are consulted only every kPollCheck polls: most waits here
+// end within a few polls, and a load on that path would delay every
+// pipeline meeting by its latency.
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;
+constexpr unsigned kPollCheck = 32;
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err)
 {
     if (mbar_try_wait(bar, parity)) return true;
-    if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
+    unsigned long long t0 = 0;
+    for (unsigned n = 1;; ++n) {
         if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if (global_ns() - t0 > kWaitNs) {
-            if (err) atomicOr(err, kErrTimeout);
-            return false;
+        if (n % kPollCheck == 0) {
+            const unsigned long long now = global_ns();
+            if (n == kPollCheck) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                if (err) atomicOr(err, kErrTimeout);
+                return false;
+            }
+            if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
         }
-        if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
     }
+}
+
+// Wait of a thread that is not on the critical path (the producer warp,
+// several stages ahead of its consumers): the same bounded test, with a
+// pause of about `ns` nanoseconds between polls so that the waiting warp
+// leaves its issue slots to the compute warps.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, unsigned* err,
+                                               unsigned ns = 128)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = 0;
+    for (unsigned n = 1;; ++n) {
+        __nanosleep(ns);
+        if (mbar_try_wait(bar, parity)) return true;
+        if (n % kPollCheck == 0) {
+            const unsigned long long now = global_ns();
+            if (n == kPollCheck) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                if (err) atomicOr(err, kErrTimeout);
+                return false;
+            }
+            if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
+        }
+    }
+}
+
+// Named CTA barrier `id` (1..15) over the `nthreads` threads (a multiple of
+// 32, whole converged warps) that execute it; orders their shared-memory
+// accesses like __syncthreads.  A hardware barrier, not a poll: it is used
+// only where every participating warp runs the same sequence of barriers
+// whatever any wait returns, so that it always completes.
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The same barrier, returning whether `pred` holds on any participating
+// thread (bar.red.or), so that the participants take one decision.
+__device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(pred)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 }  // namespace lbfe

@@ -148,7 +148,7 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
         const unsigned slot = q % unsigned(S);
         const unsigned use = q / unsigned(S);
         // the slot's previous use must be released by every compute warp
-        if (use > 0) mbar_wait(empty + slot, (use - 1) & 1u, D.err);
+        if (use > 0) mbar_wait_idle(empty + slot, (use - 1) & 1u, D.err);
         int r = T.first + p;
         r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
         // rows y0-1 and y1 serve only the phi look-ahead: g segments only
@@ -341,7 +341,7 @@ __device__ __forceinline__ void produce_end(unsigned char* smem, int nw, unsigne
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
     const unsigned slot = q % unsigned(S), use = q / unsigned(S);
-    if (use > 0) mbar_wait(empty + slot, (use - 1) & 1u, err);
+    if (use > 0) mbar_wait_idle(empty + slot, (use - 1) & 1u, err);
     if ((threadIdx.x & 31) == 0) {
         tags[slot] = -1;
         mbar_arrive(full + slot);
@@ -393,7 +393,7 @@ __device__ __forceinline__ void drain_stages(unsigned char* smem, int nw, unsign
     const unsigned n = q < unsigned(S) ? q : unsigned(S);
     for (unsigned k = 0; k < n; ++k) {
         const unsigned qq = q - 1 - k;  // last use of slot qq % S
-        mbar_wait(full + (qq % unsigned(S)), (qq / unsigned(S)) & 1u, err);
+        mbar_wait_idle(full + (qq % unsigned(S)), (qq / unsigned(S)) & 1u, err);
     }
 }
 

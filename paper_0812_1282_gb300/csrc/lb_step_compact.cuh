@@ -28,7 +28,9 @@
 //   3. collide row y (f from the stage, the phi stencil from the ring, the
 //      wall ghost rows mirrored on the fly) and store 9 f and 4 values.
 // Phases 1 -> 2 and 2 -> 3 read what other warps wrote, so the compute warps
-// meet at two mbarriers per row (bounded waits, as every wait here).
+// meet twice per row at a named CTA barrier.  That barrier is a hardware
+// wait, not a poll: every compute warp runs the same sequence of meetings
+// whatever its bounded stage waits return, so it always completes.
 #pragma once
 
 #include "lb_async.cuh"
@@ -41,13 +43,14 @@ namespace lbfe {
 constexpr int kStagesC = 3;    // stage-ring depth of the compact step
 constexpr int kEArrays = 10;   // phi word, g'_1..g'_8, sum of g'_1..g'_8
 constexpr int kESlots = 3;     // expanded rows kept
+constexpr int kComputeBarrier = 1;  // named barrier of the compute warps
 
 // Strip width of the compact step for a CTA of bx compute threads.
 __host__ __device__ constexpr int compact_strip(int bx) { return bx - 4; }
 
 // Shared memory of one CTA (byte offsets): stage barriers (full at 0, empty
-// at 64, the two compute-warp barriers at 32 and 40), S stages of 13
-// segments, the expanded-row ring, the phi ring and the word ring.
+// at 64), S stages of 13 segments, the expanded-row ring, the phi ring and
+// the word ring.
 struct StageLayoutC {
     int NW, S, W, segw, EC, PC;
     __host__ __device__ StageLayoutC(int nw, int s)
@@ -55,8 +58,6 @@ struct StageLayoutC {
     {
     }
     __host__ __device__ size_t full() const { return 0; }
-    __host__ __device__ size_t sync_a() const { return 32; }
-    __host__ __device__ size_t sync_b() const { return 40; }
     __host__ __device__ size_t empty() const { return 64; }
     __host__ __device__ size_t stages() const { return 128; }
     __host__ __device__ size_t stage_elems() const { return size_t(13) * segw; }
@@ -99,8 +100,6 @@ __device__ __forceinline__ void init_stages_c(unsigned char* smem, int NW)
             mbar_init(full + k, 1);
             mbar_init(empty + k, NW);
         }
-        mbar_init(reinterpret_cast<uint64_t*>(smem + L.sync_a()), NW);
-        mbar_init(reinterpret_cast<uint64_t*>(smem + L.sync_b()), NW);
         fence_mbar_init();
     }
     __syncthreads();
@@ -136,7 +135,7 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
     for (int p = 0; p < T.count(); ++p, ++q) {
         const unsigned slot = q % unsigned(S);
         const unsigned use = q / unsigned(S);
-        if (use > 0) mbar_wait(empty + slot, (use - 1) & 1u, D.err);
+        if (use > 0) mbar_wait_idle(empty + slot, (use - 1) & 1u, D.err);
         const int yf = p < T.npro ? -1 : y0 + (p - T.npro);          // f row (or none)
         const int ycl = p < T.npro ? T.clo + p : yf + 2;             // compact row (logical)
         const bool has_f = yf >= 0, has_c = ycl <= T.chi;
@@ -170,12 +169,11 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
 
 // ----------------------------------------------------------- consumer
 // Compute warp cw of NW; its thread t = 32 cw + lane handles expanded column
-// t, phi entry t and node column t of the strip.  sync_phase carries the
-// parities of the two compute-warp barriers across the tiles of a CTA.
+// t, phi entry t and node column t of the strip.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
-                                               int nw, int cw, unsigned& q, unsigned& sync_phase)
+                                               int nw, int cw, unsigned& q)
 {
     const int NW = NWC > 0 ? NWC : nw;
     float* __restrict__ fd = static_cast<float*>(parity ? D.f[0] : D.f[1]);
@@ -188,8 +186,6 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const int segw = L.segw, EC = L.EC, PC = L.PC;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
-    uint64_t* bar_a = reinterpret_cast<uint64_t*>(smem + L.sync_a());
-    uint64_t* bar_b = reinterpret_cast<uint64_t*>(smem + L.sync_b());
     const float* stage = reinterpret_cast<const float*>(smem + L.stages());
     float* ering = reinterpret_cast<float*>(smem + L.erings());
     float* pring = reinterpret_cast<float*>(smem + L.prings());
@@ -217,13 +213,11 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + slot_of(p));
     };
-    // all compute warps meet at barrier a (bit 0 of sync_phase) or b (bit 1):
-    // writes before the meeting are visible to reads after it
-    auto meet = [&](uint64_t* bar, unsigned bit) {
+    // all compute warps meet: writes before the meeting are visible to reads
+    // after it
+    auto meet = [&]() {
         __syncwarp();
-        if (lane == 0) mbar_arrive(bar);
-        mbar_wait(bar, (sync_phase & bit) ? 1u : 0u, D.err);
-        sync_phase ^= bit;
+        named_sync(kComputeBarrier, 32 * NW);
     };
     auto eslot = [&](int yl) -> float* {
         return ering + ((yl - y0 + 2) % kESlots) * (kEArrays * EC);
@@ -279,23 +273,23 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         wait_full(p);
         expand(p, yl);
         release(p);
-        meet(bar_a, 1u);
+        meet();
         bool any = false;
         while (pub <= y0 && ready(pub, yl)) {
             publish(pub);
             ++pub;
             any = true;
         }
-        if (any) meet(bar_b, 2u);
+        if (any) meet();
     }
     const float h2b = 2.f * prm.h_bot, h2t = 2.f * prm.h_top;
     for (int y = y0; y < y1; ++y, ++p) {
         wait_full(p);
         if (y + 2 <= T.chi) expand(p, y + 2);
-        meet(bar_a, 1u);
+        meet();
         const int yn = y + 1;
         if (!(walls && yn == ny)) publish(yn);
-        meet(bar_b, 2u);
+        meet();
         if (n_on) {
             const bool blo = walls && y == 0, bhi = walls && y == ny - 1;
             const float* sb = stage_ptr(p);

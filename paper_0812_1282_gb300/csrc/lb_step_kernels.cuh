@@ -103,13 +103,12 @@ __global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int
     init_stages_c<S>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
     const int x0 = blockIdx.x * compact_strip(32 * NW), y0 = blockIdx.y * rows;
-    unsigned q = 0, sync_phase = 0;
+    unsigned q = 0;
     if (warp == 0) {
         produce_tile_c<S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, q);
         drain_stages<float, S, NWC>(smem, NW, q, D.err);
     } else {
-        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, warp - 1, q,
-                                    sync_phase);
+        consume_tile_c<MRT, S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, warp - 1, q);
     }
 }
 
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages_c<S>(smem, NW);
     const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
-    unsigned q = 0, sync_phase = 0;
+    unsigned q = 0;
     if (warp == 0) {
         for (;;) {
             int it = 0;
@@ -151,11 +150,13 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
     } else {
         for (;;) {
             const int it = next_tag<float, S, NWC>(smem, NW, q, tags, err);
-            if (it < 0 || it >= n_items) break;
+            // one decision for all compute warps (a failed wait on one of
+            // them stops all), so that they meet at the same barriers
+            if (named_sync_or(kComputeBarrier, 32 * NW, it < 0 || it >= n_items)) break;
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
             consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, w.cols, smem, NW,
-                                        warp - 1, q, sync_phase);
+                                        warp - 1, q);
         }
     }
 }
