@@ -99,8 +99,9 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
         off = align_up(off + nodes * es, kAlign);
         max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
         max_nx = std::max<long long>(max_nx, nx[d]);
-        // strips are at least 28 columns wide (the compact step's narrowest)
-        item_cap += (long long)((nx[d] + kMinBlockX - 5) / (kMinBlockX - 4)) * ny[d];
+        // at most ceil(nx / 28) strips per row (the narrowest strip of any
+        // step is wider) and one tile row per lattice row
+        item_cap += (long long)((nx[d] + 27) / 28) * ny[d];
         pts_cap = std::max(pts_cap, 16 * (nx[d] + ny[d]));
     }
     L.item_cap = item_cap;
@@ -232,7 +233,7 @@ int build_items(lb_handle* h)
             // domain is cut into near-equal strips (multiples of 4 columns,
             // so every bulk copy stays 16-byte aligned) instead of full
             // strips and one narrow remainder
-            const int wmax = h->block_x - 4;
+            const int wmax = lbfe::compact_strip(h->block_x);
             const int k = (D.nx + wmax - 1) / wmax;
             const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
             for (int y0 = 0; y0 < D.ny; y0 += h->rows)
@@ -500,8 +501,9 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
                              cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return bail(fail(LB_ERR_CUDA, "device init failed: %s", cudaGetErrorString(e)));
-    // default launch shape: 128 threads x 32 rows (tuned by lb_autotune)
-    h->block_x = 128;
+    // default launch shape: 128 threads (64 with compact storage, whose
+    // threads take two columns each) x 32 rows (tuned by lb_autotune)
+    h->block_x = h->descs[0].compact ? 64 : 128;
     h->rows = 32;
     if (n_dom > 1) h->grid_persistent = h->sm_count * 8;
     const int rc = build_items(h);
@@ -1205,9 +1207,11 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
     // with obstacles only, no domain uses the staged kernel: nothing to tune
     const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
-    const int bxs_all[] = {64, 128, 256};
+    // compact storage: two columns per thread, so half the threads per strip
+    const int bxs_all[] = {64, 128, 256}, bxs_compact[] = {64, 96, 128};
     const int rws_all[] = {4, 8, 16, 32, 64, 128};
-    std::vector<int> bxs(bxs_all, bxs_all + 3), rws(rws_all, rws_all + 6);
+    const int* bx0 = h->descs[0].compact ? bxs_compact : bxs_all;
+    std::vector<int> bxs(bx0, bx0 + 3), rws(rws_all, rws_all + 6);
     if (!plain) {
         bxs.assign(1, h->block_x);
         rws.assign(1, h->rows);

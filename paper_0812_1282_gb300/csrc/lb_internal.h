@@ -1,6 +1,8 @@
 // Internal host/device interface of the library (not part of the C ABI).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -11,6 +13,12 @@ namespace lbfe {
 // physical nx+kXOff, nx+kXOff+1 copies of logical 0, 1 (periodic ghosts,
 // kept current by every kernel that writes populations).  pitch >= nx + 8.
 constexpr int kXOff = 4;
+
+// Node columns of one strip of the compact step (FP32, compact g storage)
+// for a CTA of bx compute threads: two columns per thread, less the four
+// halo columns the strip's phi stencil needs.  A multiple of 4 for every
+// bx that is a multiple of 32, so strips start on 16-byte boundaries.
+__host__ __device__ constexpr int compact_strip(int bx) { return 2 * bx - 4; }
 
 // One domain as the kernels see it.  Populations live in two ping-pong
 // buffers; buffer b holds f at f[b] and g at g[b], each 9 planes of

@@ -15,16 +15,18 @@
 //               = phi(r, t) + [sum_{i>0} g'_i(r - e_i) - sum_{i>0} g'_i(r)],
 // advanced as an exact integer add of the quantised bracket on the word.
 //
-// Pipeline.  A CTA of NW compute warps owns a strip of W = 32 NW - 4
-// columns, so that each of the three per-row phases below is one pass over
-// its 32 NW compute threads: W + 4 expanded columns, W + 2 phi entries and W
-// nodes.  Warp 0 (the producer) copies, for stage p of a tile, the 9 pulled f
-// segments of row y and the 4 compact segments of row y + 2 (rows above and
-// below the tile get compact-only stages).  The compute threads then, per row,
+// Pipeline.  A CTA of NW compute warps owns a strip of W = 64 NW - 4
+// columns; each compute thread takes two adjacent columns in each of the
+// three per-row phases below, so that each phase is one pass over the 32 NW
+// compute threads (W + 4 expanded columns, W + 2 phi entries, W nodes) and
+// most shared and global accesses move aligned pairs.  Warp 0 (the
+// producer) copies, for stage p of a tile, the 9 pulled f segments of row y
+// and the 4 compact segments of row y + 2 (rows above and below the tile
+// get compact-only stages).  The compute threads then, per row,
 //   1. expand the compact row they receive into the 8 outgoing g'_i, their
-//      sum and the phi word, one column each, into a CTA-wide 3-row ring;
-//   2. form phi(t+1) of row y + 1 from that ring, one entry each, into a
-//      CTA-wide 4-row phi ring (and the new words into a 2-row word ring);
+//      sum and the phi word, into a CTA-wide 3-row ring;
+//   2. form phi(t+1) of row y + 1 from that ring into a CTA-wide 4-row phi
+//      ring (and the new words into a 2-row word ring);
 //   3. collide row y (f from the stage, the phi stencil from the ring, the
 //      wall ghost rows mirrored on the fly) and store 9 f and 4 values.
 // Phases 1 -> 2 and 2 -> 3 read what other warps wrote, so the compute warps
@@ -36,25 +38,25 @@
 #include "lb_async.cuh"
 #include "lb_internal.h"
 #include "lb_node.cuh"
+#include "lb_node_x2.cuh"
 #include "lb_step.cuh"
 
 namespace lbfe {
 
-constexpr int kStagesC = 3;    // stage-ring depth of the compact step
+constexpr int kStagesC = 2;    // stage-ring depth of the compact step
 constexpr int kEArrays = 10;   // phi word, g'_1..g'_8, sum of g'_1..g'_8
 constexpr int kESlots = 3;     // expanded rows kept
 constexpr int kComputeBarrier = 1;  // named barrier of the compute warps
 
-// Strip width of the compact step for a CTA of bx compute threads.
-__host__ __device__ constexpr int compact_strip(int bx) { return bx - 4; }
-
 // Shared memory of one CTA (byte offsets): stage barriers (full at 0, empty
 // at 64), S stages of 13 segments, the expanded-row ring, the phi ring and
-// the word ring.
+// the word ring.  Every row of a ring and every segment starts on an 8-byte
+// boundary (pairs) and is padded by 4 elements beyond the last pair read.
 struct StageLayoutC {
     int NW, S, W, segw, EC, PC;
     __host__ __device__ StageLayoutC(int nw, int s)
-        : NW(nw), S(s), W(32 * nw - 4), segw(32 * nw + 4), EC(32 * nw), PC(32 * nw - 2)
+        : NW(nw), S(s), W(compact_strip(32 * nw)), segw(64 * nw + 4), EC(64 * nw + 4),
+          PC(64 * nw + 4)
     {
     }
     __host__ __device__ size_t full() const { return 0; }
@@ -168,8 +170,17 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
 }
 
 // ----------------------------------------------------------- consumer
-// Compute warp cw of NW; its thread t = 32 cw + lane handles expanded column
-// t, phi entry t and node column t of the strip.
+// Pairs of consecutive elements in shared memory: an aligned pair (one
+// 64-bit access) or any two (two 32-bit accesses).
+__device__ __forceinline__ float2 ld_pair(const float* p)
+{
+    return *reinterpret_cast<const float2*>(p);
+}
+__device__ __forceinline__ float2 ld_two(const float* p) { return make_float2(p[0], p[1]); }
+__device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+// Compute warp cw of NW; its thread t = 32 cw + lane handles expanded
+// columns, phi entries and node columns j0 = 2t and j0 + 1 of the strip.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
@@ -192,16 +203,18 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     float* wring = reinterpret_cast<float*>(smem + L.wrings());
 
     const int lane = threadIdx.x & 31;
-    const int t = 32 * cw + lane;
+    const int j0 = 2 * (32 * cw + lane);
     const TilePlanC T(y0, rows, ny, walls);
     const unsigned qb = q;
     q += unsigned(T.count());
 
     const int ncols = cols > 0 ? cols : min(L.W, nx - x0);  // node columns of this strip
-    const bool e_on = t < ncols + 4;       // expanded column t: lattice x0 - 2 + t
-    const bool p_on = t < ncols + 2;       // phi entry t: lattice x0 - 1 + t
-    const bool n_on = t < ncols;           // node column t: lattice x0 + t
-    const int x = x0 + t;
+    // a thread works on its pair when the first column of it is in use (the
+    // second one, if not, is computed from stale data and never stored)
+    const bool e_on = j0 < ncols + 4;  // expanded column j: lattice x0 - 2 + j
+    const bool p_on = j0 < ncols + 2;  // phi entry k: lattice x0 - 1 + k
+    const bool n_on = j0 < ncols;      // node column n: lattice x0 + n
+    const int x = x0 + j0;
 
     auto slot_of = [&](int p) { return (qb + unsigned(p)) % unsigned(S); };
     auto stage_ptr = [&](int p) { return stage + size_t(slot_of(p)) * L.stage_elems(); };
@@ -225,41 +238,54 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     auto rslot = [&](int y) -> float* { return pring + ((y - y0 + 1) & 3) * PC; };
     auto wslot = [&](int y) -> float* { return wring + (y & 1) * PC; };
 
-    // 1. expand compact row yl (stage p): column t, segment index t + 2
+    // 1. expand compact row yl (stage p): columns j0, j0 + 1 (segment
+    //    indices j0 + 2, j0 + 3)
     auto expand = [&](int p, int yl) {
         if (!e_on) return;
-        const float* sc = stage_ptr(p) + 9 * segw;
-        float* e = eslot(yl);
-        const int si = t + 2;
-        const float word = sc[si];
-        const float phi = G0<float>::value(word);
-        float ge[9];
-        g_equilibria<float>(phi, sc[segw + si], sc[2 * segw + si], sc[3 * segw + si], ge);
-        e[t] = word;
+        const float* sc = stage_ptr(p) + 9 * segw + j0 + 2;
+        float* e = eslot(yl) + j0;
+        const f2 w2 = ld_pair(sc);
+        f2 ge[9];
+        g_equilibria2(g0_value2(w2), ld_pair(sc + segw), ld_pair(sc + 2 * segw),
+                      ld_pair(sc + 3 * segw), ge);
+        st_pair(e, w2.v);
 #pragma unroll
-        for (int a = 1; a < 9; ++a) e[a * EC + t] = ge[a];
-        e[9 * EC + t] = g_tail_sum<float>(ge);
+        for (int a = 1; a < 9; ++a) st_pair(e + a * EC, ge[a].v);
+        st_pair(e + 9 * EC, g_tail_sum2(ge).v);
     };
-    // 2. phi(t+1) of real row r at entry t (expanded column j = t + 1)
+    // 2. phi(t+1) of real row r at entries j0, j0 + 1 (expanded columns
+    //    j0 + 1, j0 + 2); g'_i arrives from expanded column j - e_x of row
+    //    r - e_y, or, through a wall, as g'_opp(i) of the node itself
     auto publish = [&](int r) {
         if (!p_on) return;
-        const int j = t + 1;
         const bool blo = walls && r == 0, bhi = walls && r == ny - 1;
-        const float* m = eslot(r);
-        const float* b = blo ? m : eslot(r - 1);
-        const float* a = bhi ? m : eslot(r + 1);
-        const float g1 = m[1 * EC + j - 1];
-        const float g2 = m[2 * EC + j + 1];
-        const float g3 = blo ? m[4 * EC + j] : b[3 * EC + j];
-        const float g4 = bhi ? m[3 * EC + j] : a[4 * EC + j];
-        const float g5 = blo ? m[6 * EC + j] : b[5 * EC + j - 1];
-        const float g6 = bhi ? m[5 * EC + j] : a[6 * EC + j + 1];
-        const float g7 = blo ? m[8 * EC + j] : b[7 * EC + j + 1];
-        const float g8 = bhi ? m[7 * EC + j] : a[8 * EC + j - 1];
-        const float tail_in = (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
-        const float word = G0<float>::advance(m[j], tail_in - m[9 * EC + j]);
-        rslot(r)[t] = G0<float>::value(word);
-        wslot(r)[t] = word;
+        const float* m = eslot(r) + j0;
+        const f2 g1 = ld_pair(m + 1 * EC), g2 = ld_pair(m + 2 * EC + 2);
+        f2 g3, g4, g5, g6, g7, g8;
+        if (blo) {
+            g3 = ld_two(m + 4 * EC + 1);
+            g5 = ld_two(m + 6 * EC + 1);
+            g7 = ld_two(m + 8 * EC + 1);
+        } else {
+            const float* b = eslot(r - 1) + j0;
+            g3 = ld_two(b + 3 * EC + 1);
+            g5 = ld_pair(b + 5 * EC);
+            g7 = ld_pair(b + 7 * EC + 2);
+        }
+        if (bhi) {
+            g4 = ld_two(m + 3 * EC + 1);
+            g6 = ld_two(m + 5 * EC + 1);
+            g8 = ld_two(m + 7 * EC + 1);
+        } else {
+            const float* a = eslot(r + 1) + j0;
+            g4 = ld_two(a + 4 * EC + 1);
+            g6 = ld_pair(a + 6 * EC + 2);
+            g8 = ld_pair(a + 8 * EC);
+        }
+        const f2 tail_in = (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
+        const f2 word = g0_advance2(f2(ld_two(m + 1)), tail_in - f2(ld_two(m + 9 * EC + 1)));
+        st_pair(rslot(r) + j0, g0_value2(word).v);
+        st_pair(wslot(r) + j0, word.v);
     };
     // compact rows up to e expanded: is row r ready to publish?
     auto ready = [&](int r, int e) { return e >= min(r + 1, T.chi); };
@@ -292,60 +318,95 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         meet();
         if (n_on) {
             const bool blo = walls && y == 0, bhi = walls && y == ny - 1;
-            const float* sb = stage_ptr(p);
-            float f[9];
-            read9<float>(sb, segw, t + 4, blo, bhi, f);
-            const int k = t + 1;  // phi entry of the node
-            const float* sc = rslot(y);
-            const float c = sc[k], e = sc[k + 1], w = sc[k - 1];
-            float n, ne, nw, s, se, sw;
-            if (bhi) {  // ghost row ny: mirror of row ny - 2
-                const float* sq = rslot(ny - 2);
-                n = sq[k] - h2t;
-                ne = sq[k + 1] - h2t;
-                nw = sq[k - 1] - h2t;
+            // pulled f of nodes j0, j0 + 1 (segment indices j0 + 4, j0 + 5);
+            // through a wall the stage holds the node's own f_opp(i)
+            const float* sb = stage_ptr(p) + j0 + 4;
+            float2 f2x[9];
+            f2x[0] = ld_pair(sb);
+            f2x[1] = ld_two(sb + segw - 1);
+            f2x[2] = ld_two(sb + 2 * segw + 1);
+            f2x[3] = ld_pair(sb + 3 * segw);
+            f2x[4] = ld_pair(sb + 4 * segw);
+            f2x[5] = blo ? ld_pair(sb + 5 * segw) : ld_two(sb + 5 * segw - 1);
+            f2x[6] = bhi ? ld_pair(sb + 6 * segw) : ld_two(sb + 6 * segw + 1);
+            f2x[7] = blo ? ld_pair(sb + 7 * segw) : ld_two(sb + 7 * segw + 1);
+            f2x[8] = bhi ? ld_pair(sb + 8 * segw) : ld_two(sb + 8 * segw - 1);
+            // phi entries j0 .. j0 + 3 of rows y - 1, y, y + 1 (centres j0 + 1,
+            // j0 + 2); the wall ghost rows are mirrors of rows 1 and ny - 2
+            const float* rc = rslot(y) + j0;
+            const float2 c01 = ld_pair(rc), c23 = ld_pair(rc + 2);
+            float2 n01, n23, s01, s23;
+            if (bhi) {
+                const float* rq = rslot(ny - 2) + j0;
+                const float2 a01 = ld_pair(rq), a23 = ld_pair(rq + 2);
+                n01 = make_float2(a01.x - h2t, a01.y - h2t);
+                n23 = make_float2(a23.x - h2t, a23.y - h2t);
             } else {
-                const float* sp = rslot(y + 1);
-                n = sp[k];
-                ne = sp[k + 1];
-                nw = sp[k - 1];
+                const float* rq = rslot(y + 1) + j0;
+                n01 = ld_pair(rq);
+                n23 = ld_pair(rq + 2);
             }
-            if (blo) {  // ghost row -1: mirror of row 1
-                const float* sq = rslot(1);
-                s = sq[k] - h2b;
-                se = sq[k + 1] - h2b;
-                sw = sq[k - 1] - h2b;
+            if (blo) {
+                const float* rq = rslot(1) + j0;
+                const float2 a01 = ld_pair(rq), a23 = ld_pair(rq + 2);
+                s01 = make_float2(a01.x - h2b, a01.y - h2b);
+                s23 = make_float2(a23.x - h2b, a23.y - h2b);
             } else {
-                const float* sm = rslot(y - 1);
-                s = sm[k];
-                se = sm[k + 1];
-                sw = sm[k - 1];
+                const float* rq = rslot(y - 1) + j0;
+                s01 = ld_pair(rq);
+                s23 = ld_pair(rq + 2);
             }
-            float dx, dy, lap;
-            stencils<float>(c, e, w, n, s, ne, nw, se, sw, dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
-            float fo[9], uxe, uye;
-            collide_f<float, MRT>(prm, f, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, uxe, uye);
-            const float G = gamma_mu<float>(prm, c, lap);
-            const int o = y * pitch + x + kXOff;
-            const float co[4] = {wslot(y)[k], G, uxe, uye};
+            // centres (j0 + 1, j0 + 2), east (j0 + 2, j0 + 3), west (j0, j0 + 1)
+            const f2 c(c01.y, c23.x);
+            f2 dx, dy, lap;
+            stencils2(c, c23, c01, f2(n01.y, n23.x), f2(s01.y, s23.x), n23, n01, s23, s01, dx, dy,
+                      lap);
+            f2 fi[9], fo2[9], uxe, uye;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) fd[i * P + o] = fo[i];
+            for (int i = 0; i < 9; ++i) fi[i] = f2x[i];
+            collide_f2<MRT>(prm, fi, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
+            const f2 co2[4] = {f2(ld_two(wslot(y) + j0 + 1)), gamma_mu2(prm, c, lap), uxe, uye};
+            float fo[2][9], co[2][4];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co[kk];
+            for (int l = 0; l < 2; ++l) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fo[l][i] = fo2[i].lane(l);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) co[l][kk] = co2[kk].lane(l);
+            }
+            const int o = y * pitch + x + kXOff;  // even: pairs are 8-byte aligned
+            if (j0 + 1 < ncols) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    *reinterpret_cast<float2*>(fd + i * P + o) = make_float2(fo[0][i], fo[1][i]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    *reinterpret_cast<float2*>(cd + kk * P + o) = make_float2(co[0][kk], co[1][kk]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fd[i * P + o] = fo[0][i];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co[0][kk];
+            }
             // periodic ghost copies: logical 0, 1 also at nx, nx+1 and
             // logical nx-2, nx-1 also at -2, -1
-            if (x < 2) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fd[i * P + o + nx] = fo[i];
+            for (int l = 0; l < 2; ++l) {
+                const int xl = x + l;
+                if (j0 + l >= ncols) continue;
+                if (xl < 2) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + nx] = co[kk];
-            }
-            if (x >= nx - 2) {
+                    for (int i = 0; i < 9; ++i) fd[i * P + o + l + nx] = fo[l][i];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fd[i * P + o - nx] = fo[i];
+                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l + nx] = co[l][kk];
+                }
+                if (xl >= nx - 2) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o - nx] = co[kk];
+                    for (int i = 0; i < 9; ++i) fd[i * P + o + l - nx] = fo[l][i];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l - nx] = co[l][kk];
+                }
             }
         }
         release(p);

@@ -22,9 +22,10 @@ int prepare_step_f32()
 {
     int e = prepare_step_prec<float>();
     const cudaError_t r[] = {
-        allow_large_smem_compact<false, 0>(), allow_large_smem_compact<false, 2>(),
-        allow_large_smem_compact<false, 4>(), allow_large_smem_compact<false, 8>(),
-        allow_large_smem_compact<true, 0>(),  allow_large_smem_compact<true, 2>(),
+        allow_large_smem_compact<false, 0>(), allow_large_smem_compact<false, 1>(),
+        allow_large_smem_compact<false, 2>(), allow_large_smem_compact<false, 3>(), allow_large_smem_compact<false, 4>(),
+        allow_large_smem_compact<false, 8>(), allow_large_smem_compact<true, 0>(),
+        allow_large_smem_compact<true, 1>(),  allow_large_smem_compact<true, 2>(),  allow_large_smem_compact<true, 3>(),
         allow_large_smem_compact<true, 4>(),  allow_large_smem_compact<true, 8>()};
     for (cudaError_t v : r)
         if (v != cudaSuccess) e = int(v);

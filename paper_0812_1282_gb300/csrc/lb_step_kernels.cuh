@@ -204,6 +204,12 @@ cudaError_t launch_step_compact_w(const DomDesc& d, const DomDesc* d_descs,
                                   int bx, int rows, int grid_p, int* sched, cudaStream_t s)
 {
     switch (bx) {
+        case 32:
+            return launch_step_compact_t<MRT, 1>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
+        case 96:
+            return launch_step_compact_t<MRT, 3>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                                 rows, grid_p, sched, s);
         case 64:
             return launch_step_compact_t<MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
                                                  rows, grid_p, sched, s);
