@@ -15,10 +15,10 @@ namespace lbfe {
 constexpr int kXOff = 4;
 
 // Node columns of one strip of the compact step (FP32, compact g storage)
-// for a CTA of bx compute threads: two columns per thread, less the four
-// halo columns the strip's phi stencil needs.  A multiple of 4 for every
-// bx that is a multiple of 32, so strips start on 16-byte boundaries.
-__host__ __device__ constexpr int compact_strip(int bx) { return 2 * bx - 4; }
+// for a CTA of bx = 32 NW compute threads: each compute warp covers 62 new
+// columns, less the halo the phi stencil needs, rounded down to a multiple
+// of 4 so that strips start on 16-byte boundaries.
+__host__ __device__ constexpr int compact_strip(int bx) { return (62 * (bx / 32) - 2) / 4 * 4; }
 
 // One domain as the kernels see it.  Populations live in two ping-pong
 // buffers; buffer b holds f at f[b] and g at g[b], each 9 planes of

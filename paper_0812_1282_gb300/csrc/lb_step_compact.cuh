@@ -15,24 +15,33 @@
 //               = phi(r, t) + [sum_{i>0} g'_i(r - e_i) - sum_{i>0} g'_i(r)],
 // advanced as an exact integer add of the quantised bracket on the word.
 //
-// Pipeline.  A CTA of NW compute warps owns a strip of W = 64 NW - 4
-// columns; each compute thread takes two adjacent columns in each of the
-// three per-row phases below, so that each phase is one pass over the 32 NW
-// compute threads (W + 4 expanded columns, W + 2 phi entries, W nodes) and
-// most shared and global accesses move aligned pairs.  Warp 0 (the
-// producer) copies, for stage p of a tile, the 9 pulled f segments of row y
-// and the 4 compact segments of row y + 2 (rows above and below the tile
-// get compact-only stages).  The compute threads then, per row,
-//   1. expand the compact row they receive into the 8 outgoing g'_i, their
-//      sum and the phi word, into a CTA-wide 3-row ring;
-//   2. form phi(t+1) of row y + 1 from that ring into a CTA-wide 4-row phi
-//      ring (and the new words into a 2-row word ring);
-//   3. collide row y (f from the stage, the phi stencil from the ring, the
-//      wall ghost rows mirrored on the fly) and store 9 f and 4 values.
-// Phases 1 -> 2 and 2 -> 3 read what other warps wrote, so the compute warps
-// meet twice per row at a named CTA barrier.  That barrier is a hardware
-// wait, not a poll: every compute warp runs the same sequence of meetings
-// whatever its bounded stage waits return, so it always completes.
+// Pipeline.  A CTA has a producer warp and NW compute warps.  For stage p
+// of a tile the producer copies the 4 compact segments of row q = clo + p
+// and, once the tile's rows start, the 9 pulled f segments of row q - 2.
+// In the iteration of stage p every compute warp, with no help from the
+// others:
+//   1. expands compact row q over 64 columns (two per thread) into the 8
+//      outgoing g'_i of each column, in registers;
+//   2. hands the values that leave a column sideways to its neighbours with
+//      warp shuffles and sums what each column receives by source row:
+//        U(q+1) = g'_3 + g'_5 + g'_7 from row q (moving up),
+//        H(q)   = g'_1 + g'_2 from row q,
+//        D(q-1) = g'_4 + g'_6 + g'_8 from row q (moving down),
+//      (through a wall the node's own opposite populations stand in);
+//   3. forms phi(t+1) of row q - 1 = U + H + D, whose U and H it kept from
+//      the two previous iterations, into a CTA-wide 4-row phi ring (and the
+//      new words into a 4-row word ring).
+// Warp w expands the columns 62 w .. 62 w + 63 of the strip: consecutive
+// warps overlap by two columns, so every column's three sums are complete
+// in one warp (its first and last column in the other).  The compute
+// warps then meet once, at a named CTA barrier, and
+//   4. collide row q - 2 (f from the stage, the phi stencil from the ring,
+//      the wall ghost rows mirrored on the fly; two nodes per thread) and
+//      store 9 f and 4 values.
+// The strip has W = 62 NW - 2 node columns, rounded down to a multiple of 4.
+// The barrier is a hardware wait, not a poll: every compute warp runs the
+// same sequence of meetings whatever its bounded stage waits return, so it
+// always completes.
 #pragma once
 
 #include "lb_async.cuh"
@@ -43,37 +52,33 @@
 
 namespace lbfe {
 
-constexpr int kStagesC = 2;    // stage-ring depth of the compact step
-constexpr int kEArrays = 10;   // phi word, g'_1..g'_8, sum of g'_1..g'_8
-constexpr int kESlots = 3;     // expanded rows kept
-constexpr int kComputeBarrier = 1;  // named barrier of the compute warps
+constexpr int kStagesC = 4;          // stage-ring depth of the compact step
+constexpr int kComputeBarrier = 1;   // named barrier of the compute warps
 
 // Shared memory of one CTA (byte offsets): stage barriers (full at 0, empty
-// at 64), S stages of 13 segments, the expanded-row ring, the phi ring and
-// the word ring.  Every row of a ring and every segment starts on an 8-byte
-// boundary (pairs) and is padded by 4 elements beyond the last pair read.
+// at 64), S stages of 13 segments, the phi ring and the word ring.  Every
+// segment and ring row starts on a 16-byte boundary and holds 64 NW + 4
+// elements, beyond the last pair any thread reads.
 struct StageLayoutC {
-    int NW, S, W, segw, EC, PC;
+    int NW, S, W, segw, PC;
     __host__ __device__ StageLayoutC(int nw, int s)
-        : NW(nw), S(s), W(compact_strip(32 * nw)), segw(64 * nw + 4), EC(64 * nw + 4),
-          PC(64 * nw + 4)
+        : NW(nw), S(s), W(compact_strip(32 * nw)), segw(64 * nw + 4), PC(64 * nw + 4)
     {
     }
     __host__ __device__ size_t full() const { return 0; }
     __host__ __device__ size_t empty() const { return 64; }
     __host__ __device__ size_t stages() const { return 128; }
     __host__ __device__ size_t stage_elems() const { return size_t(13) * segw; }
-    __host__ __device__ size_t erings() const { return stages() + size_t(S) * stage_elems() * 4; }
-    __host__ __device__ size_t ering_elems() const { return size_t(kESlots) * kEArrays * EC; }
-    __host__ __device__ size_t prings() const { return erings() + ering_elems() * 4; }
+    __host__ __device__ size_t prings() const { return stages() + size_t(S) * stage_elems() * 4; }
     __host__ __device__ size_t wrings() const { return prings() + size_t(4) * PC * 4; }
-    __host__ __device__ size_t total() const { return wrings() + size_t(2) * PC * 4; }
+    __host__ __device__ size_t total() const { return wrings() + size_t(4) * PC * 4; }
 };
 
-// Stages of one tile: npro compact-only stages for the compact rows
-// clo .. min(y0 + 1, chi), then one stage per tile row y with the f of row
-// y and the compact row y + 2 when y + 2 <= chi.  Rows are logical (not
-// wrapped); with walls they are clipped to the lattice.
+// Stages of one tile: stage p carries the compact row q = clo + p when
+// q <= chi, and from p = npro on (q = y + 2 for tile row y) the f of row y.
+// clo = y0 - 2 and chi = y1 + 1, clipped to the lattice with walls; every
+// stage up to the tile's last row exists even where it carries nothing, so
+// that q runs without gaps.  Rows are logical (not wrapped).
 struct TilePlanC {
     int y0, y1, clo, chi, npro;
     __device__ __forceinline__ TilePlanC(int y0_, int rows, int ny, bool walls)
@@ -86,7 +91,7 @@ struct TilePlanC {
             clo = max(clo, 0);
             chi = min(chi, ny - 1);
         }
-        npro = min(y0 + 1, chi) - clo + 1;
+        npro = y0 + 2 - clo;
     }
     __device__ __forceinline__ int count() const { return npro + (y1 - y0); }
 };
@@ -179,8 +184,10 @@ __device__ __forceinline__ float2 ld_pair(const float* p)
 __device__ __forceinline__ float2 ld_two(const float* p) { return make_float2(p[0], p[1]); }
 __device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 
-// Compute warp cw of NW; its thread t = 32 cw + lane handles expanded
-// columns, phi entries and node columns j0 = 2t and j0 + 1 of the strip.
+// Compute warp cw of NW.  Its lane expands columns je, je + 1 (je = 62 cw +
+// 2 lane; strip column j is lattice column x0 - 2 + j) and collides nodes
+// jn, jn + 1 (jn = 2 (32 cw + lane); node n is lattice column x0 + n).  The
+// phi and word rings are indexed by strip column j.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
@@ -194,27 +201,23 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const bool walls = D.walls != 0;
     const NodeParams<float> prm = node_params<float>(D);
     const StageLayoutC L(NW, S);
-    const int segw = L.segw, EC = L.EC, PC = L.PC;
+    const int segw = L.segw, PC = L.PC;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full());
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty());
     const float* stage = reinterpret_cast<const float*>(smem + L.stages());
-    float* ering = reinterpret_cast<float*>(smem + L.erings());
     float* pring = reinterpret_cast<float*>(smem + L.prings());
     float* wring = reinterpret_cast<float*>(smem + L.wrings());
 
     const int lane = threadIdx.x & 31;
-    const int j0 = 2 * (32 * cw + lane);
+    const int je = 62 * cw + 2 * lane;
+    const int jn = 2 * (32 * cw + lane);
     const TilePlanC T(y0, rows, ny, walls);
     const unsigned qb = q;
     q += unsigned(T.count());
 
     const int ncols = cols > 0 ? cols : min(L.W, nx - x0);  // node columns of this strip
-    // a thread works on its pair when the first column of it is in use (the
-    // second one, if not, is computed from stale data and never stored)
-    const bool e_on = j0 < ncols + 4;  // expanded column j: lattice x0 - 2 + j
-    const bool p_on = j0 < ncols + 2;  // phi entry k: lattice x0 - 1 + k
-    const bool n_on = j0 < ncols;      // node column n: lattice x0 + n
-    const int x = x0 + j0;
+    const bool n_on = jn < ncols;
+    const int x = x0 + jn;
 
     auto slot_of = [&](int p) { return (qb + unsigned(p)) % unsigned(S); };
     auto stage_ptr = [&](int p) { return stage + size_t(slot_of(p)) * L.stage_elems(); };
@@ -232,180 +235,158 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         __syncwarp();
         named_sync(kComputeBarrier, 32 * NW);
     };
-    auto eslot = [&](int yl) -> float* {
-        return ering + ((yl - y0 + 2) % kESlots) * (kEArrays * EC);
-    };
+    // rows y0 - 1 .. y0 + 2 of a tile's window take the four ring rows in turn
     auto rslot = [&](int y) -> float* { return pring + ((y - y0 + 1) & 3) * PC; };
-    auto wslot = [&](int y) -> float* { return wring + (y & 1) * PC; };
+    auto wslot = [&](int y) -> float* { return wring + ((y - y0 + 1) & 3) * PC; };
 
-    // 1. expand compact row yl (stage p): columns j0, j0 + 1 (segment
-    //    indices j0 + 2, j0 + 3)
-    auto expand = [&](int p, int yl) {
-        if (!e_on) return;
-        const float* sc = stage_ptr(p) + 9 * segw + j0 + 2;
-        float* e = eslot(yl) + j0;
-        const f2 w2 = ld_pair(sc);
-        f2 ge[9];
-        g_equilibria2(g0_value2(w2), ld_pair(sc + segw), ld_pair(sc + 2 * segw),
-                      ld_pair(sc + 3 * segw), ge);
-        st_pair(e, w2.v);
-#pragma unroll
-        for (int a = 1; a < 9; ++a) st_pair(e + a * EC, ge[a].v);
-        st_pair(e + 9 * EC, g_tail_sum2(ge).v);
-    };
-    // 2. phi(t+1) of real row r at entries j0, j0 + 1 (expanded columns
-    //    j0 + 1, j0 + 2); g'_i arrives from expanded column j - e_x of row
-    //    r - e_y, or, through a wall, as g'_opp(i) of the node itself
-    auto publish = [&](int r) {
-        if (!p_on) return;
-        const bool blo = walls && r == 0, bhi = walls && r == ny - 1;
-        const float* m = eslot(r) + j0;
-        const f2 g1 = ld_pair(m + 1 * EC), g2 = ld_pair(m + 2 * EC + 2);
-        f2 g3, g4, g5, g6, g7, g8;
-        if (blo) {
-            g3 = ld_two(m + 4 * EC + 1);
-            g5 = ld_two(m + 6 * EC + 1);
-            g7 = ld_two(m + 8 * EC + 1);
-        } else {
-            const float* b = eslot(r - 1) + j0;
-            g3 = ld_two(b + 3 * EC + 1);
-            g5 = ld_pair(b + 5 * EC);
-            g7 = ld_pair(b + 7 * EC + 2);
-        }
-        if (bhi) {
-            g4 = ld_two(m + 3 * EC + 1);
-            g6 = ld_two(m + 5 * EC + 1);
-            g8 = ld_two(m + 7 * EC + 1);
-        } else {
-            const float* a = eslot(r + 1) + j0;
-            g4 = ld_two(a + 4 * EC + 1);
-            g6 = ld_pair(a + 6 * EC + 2);
-            g8 = ld_pair(a + 8 * EC);
-        }
-        const f2 tail_in = (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
-        const f2 word = g0_advance2(f2(ld_two(m + 1)), tail_in - f2(ld_two(m + 9 * EC + 1)));
-        st_pair(rslot(r) + j0, g0_value2(word).v);
-        st_pair(wslot(r) + j0, word.v);
-    };
-    // compact rows up to e expanded: is row r ready to publish?
-    auto ready = [&](int r, int e) { return e >= min(r + 1, T.chi); };
-
-    const int y1 = T.y1;
-    int pub = (walls && y0 == 0) ? 0 : y0 - 1;
-    int p = 0;
-    // prologue: compact-only stages; publish rows y0-1 (unless a wall ghost) and y0
-    for (; p < T.npro; ++p) {
-        const int yl = T.clo + p;
-        wait_full(p);
-        expand(p, yl);
-        release(p);
-        meet();
-        bool any = false;
-        while (pub <= y0 && ready(pub, yl)) {
-            publish(pub);
-            ++pub;
-            any = true;
-        }
-        if (any) meet();
-    }
+    // real rows whose phi(t+1) the tile needs (wall ghost rows are mirrors)
+    const int pub_lo = (walls && y0 == 0) ? 0 : y0 - 1;
+    const int pub_hi = walls ? min(T.y1, ny - 1) : T.y1;
+    // the sums of rows q and q - 1 carried from iteration to iteration
+    const f2 zero(0.f);
+    f2 u_next = zero;                 // U(q + 1)
+    f2 uh = zero, wd = zero, tl = zero;  // U + H, phi word, tail of row q - 1
+    f2 d_wall = zero;                 // D of the top wall row, from that row itself
     const float h2b = 2.f * prm.h_bot, h2t = 2.f * prm.h_top;
-    for (int y = y0; y < y1; ++y, ++p) {
+    const unsigned kAll = 0xffffffffu;
+    for (int p = 0; p < T.count(); ++p) {
+        const int qr = T.clo + p;  // compact row of this stage
         wait_full(p);
-        if (y + 2 <= T.chi) expand(p, y + 2);
+        f2 d_pub = d_wall;         // D of row qr - 1
+        f2 uh_q = zero, wd_q = zero, tl_q = zero;
+        const bool has_c = qr <= T.chi;
+        if (has_c) {
+            // 1. expand (every lane: all take part in the shuffles)
+            const float* sc = stage_ptr(p) + 9 * segw + je + 2;
+            wd_q = ld_pair(sc);
+            f2 ge[9];
+            g_equilibria2(g0_value2(wd_q), ld_pair(sc + segw), ld_pair(sc + 2 * segw),
+                          ld_pair(sc + 3 * segw), ge);
+            tl_q = g_tail_sum2(ge);
+            // 2. what enters column je from the left and je + 1 from the right
+            const f2 g5l(__shfl_up_sync(kAll, ge[5].v.y, 1), ge[5].v.x);
+            const f2 g1l(__shfl_up_sync(kAll, ge[1].v.y, 1), ge[1].v.x);
+            const f2 g8l(__shfl_up_sync(kAll, ge[8].v.y, 1), ge[8].v.x);
+            const f2 g7r(ge[7].v.y, __shfl_down_sync(kAll, ge[7].v.x, 1));
+            const f2 g2r(ge[2].v.y, __shfl_down_sync(kAll, ge[2].v.x, 1));
+            const f2 g6r(ge[6].v.y, __shfl_down_sync(kAll, ge[6].v.x, 1));
+            const f2 h_q = g1l + g2r;
+            const f2 u_q = (walls && qr == 0) ? (ge[4] + ge[6]) + ge[8] : u_next;
+            uh_q = u_q + h_q;
+            d_pub = (ge[4] + g6r) + g8l;
+            u_next = (ge[3] + g5l) + g7r;
+            if (walls && qr == ny - 1) d_wall = (ge[3] + ge[5]) + ge[7];
+        }
+        // 3. phi(t+1) of row qr - 1
+        const int r = qr - 1;
+        if (r >= pub_lo && r <= pub_hi) {
+            const f2 word = g0_advance2(wd, (uh + d_pub) - tl);
+            const f2 phi = g0_value2(word);
+            float* pr = rslot(r) + je;
+            float* wr = wslot(r) + je;
+            // a warp's first and last column are complete in its neighbours
+            if (lane > 0 && lane < 31) {
+                st_pair(pr, phi.v);
+                st_pair(wr, word.v);
+            } else if (lane == 0) {
+                pr[1] = phi.v.y;
+                wr[1] = word.v.y;
+            } else {
+                pr[0] = phi.v.x;
+                wr[0] = word.v.x;
+            }
+        }
+        uh = uh_q;
+        wd = wd_q;
+        tl = tl_q;
+        if (p < T.npro) {
+            release(p);
+            meet();
+            continue;
+        }
         meet();
-        const int yn = y + 1;
-        if (!(walls && yn == ny)) publish(yn);
-        meet();
+        // 4. collide row y = qr - 2
+        const int y = qr - 2;
         if (n_on) {
             const bool blo = walls && y == 0, bhi = walls && y == ny - 1;
-            // pulled f of nodes j0, j0 + 1 (segment indices j0 + 4, j0 + 5);
+            // pulled f of nodes jn, jn + 1 (segment indices jn + 4, jn + 5);
             // through a wall the stage holds the node's own f_opp(i)
-            const float* sb = stage_ptr(p) + j0 + 4;
-            float2 f2x[9];
-            f2x[0] = ld_pair(sb);
-            f2x[1] = ld_two(sb + segw - 1);
-            f2x[2] = ld_two(sb + 2 * segw + 1);
-            f2x[3] = ld_pair(sb + 3 * segw);
-            f2x[4] = ld_pair(sb + 4 * segw);
-            f2x[5] = blo ? ld_pair(sb + 5 * segw) : ld_two(sb + 5 * segw - 1);
-            f2x[6] = bhi ? ld_pair(sb + 6 * segw) : ld_two(sb + 6 * segw + 1);
-            f2x[7] = blo ? ld_pair(sb + 7 * segw) : ld_two(sb + 7 * segw + 1);
-            f2x[8] = bhi ? ld_pair(sb + 8 * segw) : ld_two(sb + 8 * segw - 1);
-            // phi entries j0 .. j0 + 3 of rows y - 1, y, y + 1 (centres j0 + 1,
-            // j0 + 2); the wall ghost rows are mirrors of rows 1 and ny - 2
-            const float* rc = rslot(y) + j0;
-            const float2 c01 = ld_pair(rc), c23 = ld_pair(rc + 2);
-            float2 n01, n23, s01, s23;
+            const float* sb = stage_ptr(p) + jn + 4;
+            f2 fi[9];
+            fi[0] = ld_pair(sb);
+            fi[1] = ld_two(sb + segw - 1);
+            fi[2] = ld_two(sb + 2 * segw + 1);
+            fi[3] = ld_pair(sb + 3 * segw);
+            fi[4] = ld_pair(sb + 4 * segw);
+            fi[5] = blo ? ld_pair(sb + 5 * segw) : ld_two(sb + 5 * segw - 1);
+            fi[6] = bhi ? ld_pair(sb + 6 * segw) : ld_two(sb + 6 * segw + 1);
+            fi[7] = blo ? ld_pair(sb + 7 * segw) : ld_two(sb + 7 * segw + 1);
+            fi[8] = bhi ? ld_pair(sb + 8 * segw) : ld_two(sb + 8 * segw - 1);
+            // phi of strip columns jn + 1 .. jn + 4 of rows y - 1, y, y + 1
+            // (centres jn + 2, jn + 3); the wall ghost rows mirror rows 1 and
+            // ny - 2 less 2h
+            auto row3 = [&](const float* rw, f2& w, f2& c, f2& e) {
+                const float2 a = ld_pair(rw + jn), b = ld_pair(rw + jn + 2),
+                             d = ld_pair(rw + jn + 4);
+                w = f2(a.y, b.x);
+                c = f2(b);
+                e = f2(b.y, d.x);
+            };
+            f2 cw_, cc, ce, nw_, nc, ne, sw, sc_, se;
+            row3(rslot(y), cw_, cc, ce);
             if (bhi) {
-                const float* rq = rslot(ny - 2) + j0;
-                const float2 a01 = ld_pair(rq), a23 = ld_pair(rq + 2);
-                n01 = make_float2(a01.x - h2t, a01.y - h2t);
-                n23 = make_float2(a23.x - h2t, a23.y - h2t);
+                row3(rslot(ny - 2), nw_, nc, ne);
+                const f2 h(h2t);
+                nw_ = nw_ - h;
+                nc = nc - h;
+                ne = ne - h;
             } else {
-                const float* rq = rslot(y + 1) + j0;
-                n01 = ld_pair(rq);
-                n23 = ld_pair(rq + 2);
+                row3(rslot(y + 1), nw_, nc, ne);
             }
             if (blo) {
-                const float* rq = rslot(1) + j0;
-                const float2 a01 = ld_pair(rq), a23 = ld_pair(rq + 2);
-                s01 = make_float2(a01.x - h2b, a01.y - h2b);
-                s23 = make_float2(a23.x - h2b, a23.y - h2b);
+                row3(rslot(1), sw, sc_, se);
+                const f2 h(h2b);
+                sw = sw - h;
+                sc_ = sc_ - h;
+                se = se - h;
             } else {
-                const float* rq = rslot(y - 1) + j0;
-                s01 = ld_pair(rq);
-                s23 = ld_pair(rq + 2);
+                row3(rslot(y - 1), sw, sc_, se);
             }
-            const bool s2 = D.step2 && (blo || bhi);
-            // centres (j0 + 1, j0 + 2), east (j0 + 2, j0 + 3), west (j0, j0 + 1)
-            const f2 c(c01.y, c23.x);
             f2 dx, dy, lap;
-            stencils2(c, c23, c01, f2(n01.y, n23.x), f2(s01.y, s23.x), n23, n01, s23, s01, dx, dy,
-                      lap);
-            f2 fi[9], fo2[9], uxe, uye;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fi[i] = f2x[i];
-            collide_f2<MRT>(prm, fi, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
-            const f2 co2[4] = {f2(ld_two(wslot(y) + j0 + 1)), gamma_mu2(prm, c, lap), uxe, uye};
-            float fo[2][9], co[2][4];
-#pragma unroll
-            for (int l = 0; l < 2; ++l) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) fo[l][i] = fo2[i].lane(l);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) co[l][kk] = co2[kk].lane(l);
-            }
+            stencils2(cc, ce, cw_, nc, sc_, ne, nw_, se, sw, dx, dy, lap);
+            const bool s2 = D.step2 && (blo || bhi);
+            f2 fo2[9], uxe, uye;
+            collide_f2<MRT>(prm, fi, cc, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
+            const f2 co2[4] = {f2(ld_pair(wslot(y) + jn + 2)), gamma_mu2(prm, cc, lap), uxe, uye};
             const int o = y * pitch + x + kXOff;  // even: pairs are 8-byte aligned
-            if (j0 + 1 < ncols) {
+            if (jn + 1 < ncols) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    *reinterpret_cast<float2*>(fd + i * P + o) = make_float2(fo[0][i], fo[1][i]);
+                for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(fd + i * P + o) = fo2[i].v;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    *reinterpret_cast<float2*>(cd + kk * P + o) = make_float2(co[0][kk], co[1][kk]);
+                for (int kk = 0; kk < 4; ++kk) *reinterpret_cast<float2*>(cd + kk * P + o) = co2[kk].v;
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fd[i * P + o] = fo[0][i];
+                for (int i = 0; i < 9; ++i) fd[i * P + o] = fo2[i].v.x;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co[0][kk];
+                for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co2[kk].v.x;
             }
             // periodic ghost copies: logical 0, 1 also at nx, nx+1 and
             // logical nx-2, nx-1 also at -2, -1
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 const int xl = x + l;
-                if (j0 + l >= ncols) continue;
+                if (jn + l >= ncols) continue;
                 if (xl < 2) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fd[i * P + o + l + nx] = fo[l][i];
+                    for (int i = 0; i < 9; ++i) fd[i * P + o + l + nx] = fo2[i].lane(l);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l + nx] = co[l][kk];
+                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l + nx] = co2[kk].lane(l);
                 }
                 if (xl >= nx - 2) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fd[i * P + o + l - nx] = fo[l][i];
+                    for (int i = 0; i < 9; ++i) fd[i * P + o + l - nx] = fo2[i].lane(l);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l - nx] = co[l][kk];
+                    for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l - nx] = co2[kk].lane(l);
                 }
             }
         }
