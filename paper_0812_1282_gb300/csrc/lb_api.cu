@@ -1208,10 +1208,10 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     // with obstacles only, no domain uses the staged kernel: nothing to tune
     const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
     // compact storage: two columns per thread, so half the threads per strip
-    const int bxs_all[] = {64, 128, 256}, bxs_compact[] = {64, 96, 128};
+    const int bxs_all[] = {64, 128, 256}, bxs_compact[] = {32, 64, 96, 128};
     const int rws_all[] = {4, 8, 16, 32, 64, 128};
-    const int* bx0 = h->descs[0].compact ? bxs_compact : bxs_all;
-    std::vector<int> bxs(bx0, bx0 + 3), rws(rws_all, rws_all + 6);
+    std::vector<int> bxs(bxs_all, bxs_all + 3), rws(rws_all, rws_all + 6);
+    if (h->descs[0].compact) bxs.assign(bxs_compact, bxs_compact + 4);
     if (!plain) {
         bxs.assign(1, h->block_x);
         rws.assign(1, h->rows);

@@ -52,7 +52,7 @@
 
 namespace lbfe {
 
-constexpr int kStagesC = 4;          // stage-ring depth of the compact step
+constexpr int kStagesC = 3;          // stage-ring depth of the compact step
 constexpr int kComputeBarrier = 1;   // named barrier of the compute warps
 
 // Shared memory of one CTA (byte offsets): stage barriers (full at 0, empty
