@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 import lbinputs  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
+FP64_OPS_PER_CLK_SM = 2  # GB300: 2 FP64 operations (DFMA, DADD, DMUL) per clock per SM
 BYTES_PER_NODE = {"fp32": 144, "fp64": 288, "fp32c": 104}  # fp32c: compact g storage
 
 
@@ -62,20 +62,35 @@ def measured_peaks():
         return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
 
 
-def profile_traffic(name: str):
-    """DRAM bytes per launch recorded by an ncu capture (profiles/<name>.txt,
-    lines 'source_hash: ...' and 'dram_bytes_per_launch: ...'); None when the
-    kernel sources changed since the capture."""
+def profile_value(name: str, key: str):
+    """A number recorded from an ncu capture (profiles/<name>.txt, lines
+    'source_hash: ...' and '<key>: ...'); None when the kernel sources
+    changed since the capture."""
     path = os.path.join(ROOT, "profiles", name + ".txt")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    m_val = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash():
         return None
-    return float(m_bytes.group(1))
+    return float(m_val.group(1))
+
+
+def profile_traffic(name: str):
+    """DRAM bytes per launch of an ncu capture (None when stale)."""
+    return profile_value(name, "dram_bytes_per_launch")
+
+
+def sm_max_mhz() -> float:
+    """Maximum SM clock of GPU 0 (nvidia-smi), 2070 MHz if unreadable."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", "0"], capture_output=True, text=True, timeout=30).stdout
+        return float(out.split()[0])
+    except Exception:
+        return 2070.0
 
 
 class ClockSampler:
@@ -251,18 +266,45 @@ def run_e2e(lbf, torch, steps, compact=False):
     return dict(seconds=dt, h2d=h2d, d2h=d2h, finite=ok)
 
 
-def run_fp64(lbf, torch, steps):
+def run_fp64(lbf, torch, steps, size=None, tile=None):
+    """The headline workload in FP64 storage and arithmetic.  On this GPU
+    the step is bound by the FP64 pipe, so besides its bytes it reports the
+    pipe's operations per second against its peak (2 per clock per SM), with
+    the operations per node counted by ncu
+    (profiles/lb_step_mrt_fp64_2048.txt)."""
     c = lbinputs.SPINODAL_8192
-    n = c["nx"] * c["ny"]
+    side = size or c["nx"]
+    n = side * side
     p = lbf.params(precision="fp64", **c["params"])
-    sim = lbf.Lattice(p, c["nx"], c["ny"])
+    sim = lbf.Lattice(p, side, side)
     sim.init_random(c["amp"], c["seed"])
-    tile = sim.autotune(reps=1)
+    if tile:
+        sim.set_tile(*tile)
+    else:
+        tile = sim.autotune(reps=1)
     sim.step(2)
     dt = time_steps(sim, steps, torch)
     sim.close()
-    return dict(mlups=n * steps / dt / 1e6, seconds_per_step=dt / steps, tile=list(tile[:2]),
-                gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9)
+    res = dict(mlups=n * steps / dt / 1e6, seconds_per_step=dt / steps, tile=list(tile[:2]),
+               gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9, bound="alu")
+    # the FP64 pipe takes one DADD, DMUL or DFMA per slot: its roofline counts
+    # those operations (a DFMA is two flops, the others one)
+    opn = profile_value("lb_step_mrt_fp64_2048", "fp64_ops_per_node")
+    fpn = profile_value("lb_step_mrt_fp64_2048", "fp64_flops_per_node")
+    res["fp64_ops_per_node"] = opn
+    res["fp64_flops_per_node"] = fpn
+    if opn is not None and fpn is not None:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        ghz = sm_max_mhz() / 1e3
+        rate = n * steps / dt
+        res.update(achieved_gops=round(rate * opn / 1e9, 1),
+                   peak_gops=round(FP64_OPS_PER_CLK_SM * sms * ghz, 1),
+                   frac=round(rate * opn / 1e9 / (FP64_OPS_PER_CLK_SM * sms * ghz), 4),
+                   achieved_tflops=round(rate * fpn / 1e12, 4),
+                   peak_tflops=round(2 * FP64_OPS_PER_CLK_SM * sms * ghz / 1e3, 4),
+                   peak_source="derived: 2 FP64 pipe operations per clock per SM x SMs x "
+                               "max SM clock")
+    return res
 
 
 def run_capillary(lbf, torch, steps=None):
@@ -431,6 +473,9 @@ def ours(args):
         # one extra workload alone (profiling aid): its JSON object only
         if args.only == "batched":
             res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact")
+        elif args.only == "fp64":
+            tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
+            res = run_fp64(lbf, torch, max(3, args.steps), size=args.size, tile=tile)
         else:
             res = run_capillary(lbf, torch, max(1000, args.steps))
         print(json.dumps({"workload": args.only, **res}), flush=True)
@@ -500,10 +545,7 @@ def ours(args):
                 extras["full_storage"] = {"error": str(exc)}
             torch.cuda.empty_cache()
         try:
-            fp64 = run_fp64(lbf, torch, max(4, args.steps // 20))
-            fp64["bound"] = "alu"
-            fp64["alu_peak_tflops_nominal"] = FP64_NOMINAL_TFLOPS
-            extras["fp64"] = fp64
+            extras["fp64"] = run_fp64(lbf, torch, max(4, args.steps // 20))
         except Exception as exc:  # report, do not hide
             extras["fp64"] = {"error": str(exc)}
         torch.cuda.empty_cache()
@@ -622,7 +664,7 @@ def main():
                     help="fixed launch shape BXxROWS instead of autotuning (profiling aid)")
     ap.add_argument("--storage", choices=("full", "compact"), default="compact",
                     help="g storage of the headline lattice (compact: phi, Gamma mu, u_eq)")
-    ap.add_argument("--only", choices=("batched", "capillary"), default=None,
+    ap.add_argument("--only", choices=("batched", "capillary", "fp64"), default=None,
                     help="run one extra workload alone for --steps steps (profiling aid)")
     ap.add_argument("--experiment", choices=("ramp",), default=None,
                     help="run a physics experiment instead of the benchmark and print its "
