@@ -20,6 +20,11 @@ stated; x periodic; bounce-back walls at y = 0 and y = ny - 1):
                    from column 200 on, h(60 deg) on the channel walls,
                    neutral elsewhere; MRT, tau_alpha 1.5, tau_beta 0.6;
                    100000 steps, front tracked every 500.
+  STRIPE_28x15     the spurious-current set-up of Sec. IV.A: a stripe of
+                   alpha (columns 7..20, tanh edges of width sqrt(2 kappa/a))
+                   across the channel between neutral walls; BGK and MRT at
+                   tau 10 / 10 (the paper's case) and at viscosity ratios
+                   12.5 (tau 3 / 0.7) and 10 (1.5 / 0.6); 20000 steps.
   SPINODAL_8192    MRT, tau_alpha 1.5, tau_beta 0.6, neutral walls,
                    phi uniform in [-0.1, 0.1) from SplitMix64 seed 12345
                    (node (x, y) takes draw y*nx + x); FP32 and FP64.
@@ -93,6 +98,10 @@ CAPILLARY_1000x120 = dict(nx=1000, ny=120, res_len=200, ch_w=40, theta=60.0, h_b
                           steps=100000, every=500,
                           params=dict(BASE, collision="mrt", tau_alpha=1.5, tau_beta=0.6,
                                       h_bottom=0.0, h_top=0.0))
+
+STRIPE_28x15 = dict(nx=28, ny=15, xa=7.0, xb=21.0, steps=20000,
+                    taus=((10.0, 10.0), (3.0, 0.7), (1.5, 0.6)),
+                    params=dict(BASE, h_bottom=0.0, h_top=0.0))
 
 SPINODAL_8192 = dict(nx=8192, ny=8192, amp=0.1, seed=12345, steps=1000,
                      sub=512,

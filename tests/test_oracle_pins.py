@@ -657,3 +657,72 @@ def test_lookup_table_run_converges_to_exact(oracle_mod):
     fine = np.abs(runs[10000] - runs[0]).max()
     coarse = np.abs(runs[3] - runs[0]).max()
     assert fine < 1e-3 and coarse > 20 * fine
+
+
+# ---------------------------------------------------- stripe (Sec. IV.A)
+def _stripe_phi0(c, p):
+    """tanh edges at xa (rising) and xb (falling), each over its half of the
+    period, so that the profile shifted by half the period is exactly its
+    negative."""
+    ell = math.sqrt(2 * p.kappa / p.a)
+    x = np.arange(c["nx"], dtype=float)
+    half = c["nx"] // 2
+    prof = np.where(x < half, np.tanh((x - c["xa"]) / ell), -np.tanh((x - c["xb"]) / ell))
+    return np.tile(prof, (c["ny"], 1))
+
+
+def _left_edge(row):
+    """x of the phi = 0 crossing of the stripe's left edge (linear between
+    the two nodes around it)."""
+    for i in range(1, row.size // 2):
+        if row[i - 1] < 0.0 <= row[i]:
+            return i - 1 + (-row[i - 1]) / (row[i] - row[i - 1])
+    return float("nan")
+
+
+def stripe_run(oracle_mod, coll, ta, tb, steps=None):
+    """Steady state of the stripe: (phi, max |u|, bulge), the bulge being
+    the left edge's x at mid-height less its x on the wall row (negative:
+    the alpha stripe is wider in the middle, barrel shaped)."""
+    c = lbinputs.STRIPE_28x15
+    p = oracle_mod.params(collision=coll, tau_alpha=ta, tau_beta=tb, **c["params"])
+    lat = oracle_mod.OracleLattice(p, c["nx"], c["ny"])
+    lat.init_phi(_stripe_phi0(c, p))
+    lat.step(steps or c["steps"])
+    _, ph, ux, uy = lat.moments()
+    bulge = _left_edge(ph[c["ny"] // 2]) - _left_edge(ph[0])
+    return ph, float(np.hypot(ux, uy).max()), bulge
+
+
+def test_stripe_spurious_current_is_of_order_1e_3(oracle_mod):
+    """Sec. IV.A: the 28 x 15 stripe at tau = 10 between neutral walls
+    settles with spurious velocities of order 10^-3 c, and with equal
+    viscosities its edges stay straight (the 90 degree angle)."""
+    _, umax, bulge = stripe_run(oracle_mod, "bgk", 10.0, 10.0)
+    assert 1e-4 < umax < 1e-2
+    assert abs(bulge) < 1e-4
+
+
+def test_stripe_barrel_shape_bgk_not_mrt(oracle_mod):
+    """Sec. IV.A: with tau_alpha > tau_beta the BGK stripe becomes barrel
+    shaped (at the paper's ratio 12.5).  MRT with Step 2, the paper's cure,
+    keeps the edges much straighter."""
+    _, _, b_bgk = stripe_run(oracle_mod, "bgk", 3.0, 0.7)
+    _, _, b_mrt = stripe_run(oracle_mod, "mrt", 3.0, 0.7)
+    assert b_bgk < -0.2
+    assert abs(b_mrt) < 0.5 * abs(b_bgk)
+
+
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+def test_stripe_phase_swap_antisymmetry(oracle_mod, coll):
+    """phi -> -phi with tau_alpha <-> tau_beta maps the stripe onto its
+    complement (both 14 columns wide): mu and g^eq are odd in phi, f^eq is
+    even, so the two runs are mirror images (to the rounding of the two
+    forms of tau(phi)) and the bulge changes sign."""
+    c = lbinputs.STRIPE_28x15
+    ph1, u1, b1 = stripe_run(oracle_mod, coll, 1.5, 0.6, steps=4000)
+    ph2, u2, b2 = stripe_run(oracle_mod, coll, 0.6, 1.5, steps=4000)
+    shift = int(c["xb"] - c["xa"])
+    assert np.abs(np.roll(ph1, shift, axis=1) + ph2).max() < 1e-10
+    assert abs(b1 + b2) < 1e-9 and abs(b1) > 1e-3
+    assert u1 == pytest.approx(u2, rel=1e-9)
