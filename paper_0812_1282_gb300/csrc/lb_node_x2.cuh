@@ -1,7 +1,7 @@
 // The FP32 per-node arithmetic of lb_node.cuh on two nodes at once, with
 // the packed FP32 add, multiply and fused multiply-add of sm_100 and later
-// (one instruction for both lanes; the compact step is bound by instruction
-// issue, and most of its arithmetic is this).  Each lane evaluates the same
+// (one instruction for both lanes, half the issue slots of the scalar
+// form).  Each lane evaluates the same
 // formulas as the scalar path for its own node (Appendix A equilibria,
 // Eq. best stencils, Eq. chempot, Eq. tau, Steps 1-3 of Sec. V), with the
 // same unbiased divisions by small constants; products that feed a sum are
@@ -30,14 +30,16 @@ __device__ __forceinline__ f2 operator-(f2 a, f2 b)
     return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v));
 }
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 operator*(float k, f2 b) { return f2(__fmul2_rn(make_float2(k, k), b.v)); }
+__device__ __forceinline__ f2 operator*(float k, f2 b)
+{
+    return f2(__fmul2_rn(make_float2(k, k), b.v));
+}
 // a * b + c, one rounding
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
 __device__ __forceinline__ f2 fma2(float k, f2 b, f2 c)
 {
     return f2(__ffma2_rn(make_float2(k, k), b.v, c.v));
 }
-__device__ __forceinline__ f2 select2(bool c, f2 a, f2 b) { return c ? a : b; }
 
 // x / K, unbiased (the residual step of div_const<K, float>)
 template <int K>
@@ -54,7 +56,8 @@ __device__ __forceinline__ f2 rcp2(f2 x) { return f2(__frcp_rn(x.v.x), __frcp_rn
 // G0<float>::value / advance lane by lane (integer words)
 __device__ __forceinline__ f2 g0_value2(f2 w)
 {
-    return 0x1p-29f * f2(__int2float_rn(__float_as_int(w.v.x)), __int2float_rn(__float_as_int(w.v.y)));
+    return 0x1p-29f *
+           f2(__int2float_rn(__float_as_int(w.v.x)), __int2float_rn(__float_as_int(w.v.y)));
 }
 __device__ __forceinline__ f2 g0_advance2(f2 w, f2 d)
 {
