@@ -17,7 +17,7 @@
 //
 // Pipeline.  A CTA has a producer warp and NW compute warps.  For stage p
 // of a tile the producer copies the 4 compact segments of row q = clo + p
-// and, once the tile's rows start, the 9 pulled f segments of row q - 2.
+// and, once the tile's rows start, the 9 pulled f segments of row q - 3.
 // In the iteration of stage p every compute warp, with no help from the
 // others:
 //   1. expands compact row q over 64 columns (two per thread) into the 8
@@ -33,11 +33,14 @@
 //      new words into a 4-row word ring).
 // Warp w expands the columns 62 w .. 62 w + 63 of the strip: consecutive
 // warps overlap by two columns, so every column's three sums are complete
-// in one warp (its first and last column in the other).  The compute
-// warps then meet once, at a named CTA barrier, and
-//   4. collide row q - 2 (f from the stage, the phi stencil from the ring,
-//      the wall ghost rows mirrored on the fly; two nodes per thread) and
-//      store 9 f and 4 values.
+// in one warp (its first and last column in the other).  In the same
+// iteration each compute warp
+//   4. collides row q - 3 (f from the stage, the phi stencil of rows q - 4
+//      .. q - 2 from the ring, the wall ghost rows mirrored on the fly; two
+//      nodes per thread) and stores 9 f and 4 values.
+// Steps 1-3 and step 4 touch different rows, so a warp can overlap them;
+// the compute warps meet once per iteration, at a named CTA barrier, after
+// which the phi of row q - 1 is visible to every warp.
 // The strip has W = 62 NW - 2 node columns, rounded down to a multiple of 4.
 // The barrier is a hardware wait, not a poll: every compute warp runs the
 // same sequence of meetings whatever its bounded stage waits return, so it
@@ -75,7 +78,7 @@ struct StageLayoutC {
 };
 
 // Stages of one tile: stage p carries the compact row q = clo + p when
-// q <= chi, and from p = npro on (q = y + 2 for tile row y) the f of row y.
+// q <= chi, and from p = npro on (q = y + 3 for tile row y) the f of row y.
 // clo = y0 - 2 and chi = y1 + 1, clipped to the lattice with walls; every
 // stage up to the tile's last row exists even where it carries nothing, so
 // that q runs without gaps.  Rows are logical (not wrapped).
@@ -91,7 +94,7 @@ struct TilePlanC {
             clo = max(clo, 0);
             chi = min(chi, ny - 1);
         }
-        npro = y0 + 2 - clo;
+        npro = y0 + 3 - clo;
     }
     __device__ __forceinline__ int count() const { return npro + (y1 - y0); }
 };
@@ -143,8 +146,8 @@ __device__ __forceinline__ void produce_tile_c(const DomDesc& D, int parity, int
         const unsigned slot = q % unsigned(S);
         const unsigned use = q / unsigned(S);
         if (use > 0) mbar_wait_idle(empty + slot, (use - 1) & 1u, D.err);
-        const int yf = p < T.npro ? -1 : y0 + (p - T.npro);          // f row (or none)
-        const int ycl = p < T.npro ? T.clo + p : yf + 2;             // compact row (logical)
+        const int yf = p < T.npro ? -1 : y0 + (p - T.npro);  // f row (or none)
+        const int ycl = T.clo + p;                            // compact row (logical)
         const bool has_f = yf >= 0, has_c = ycl <= T.chi;
         if (lane == 0) {
             if (tags && p == 0) tags[slot] = tag;
@@ -299,15 +302,10 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         uh = uh_q;
         wd = wd_q;
         tl = tl_q;
-        if (p < T.npro) {
-            release(p);
-            meet();
-            continue;
-        }
-        meet();
-        // 4. collide row y = qr - 2
-        const int y = qr - 2;
-        if (n_on) {
+        // 4. collide row y = qr - 3 (rows q - 4 .. q - 2 of the ring were
+        //    published before the previous meeting)
+        const int y = qr - 3;
+        if (p >= T.npro && n_on) {
             const bool blo = walls && y == 0, bhi = walls && y == ny - 1;
             // pulled f of nodes jn, jn + 1 (segment indices jn + 4, jn + 5);
             // through a wall the stage holds the node's own f_opp(i)
@@ -391,6 +389,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             }
         }
         release(p);
+        meet();
     }
 }
 
