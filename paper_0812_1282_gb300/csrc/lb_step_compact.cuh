@@ -238,7 +238,8 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         __syncwarp();
         named_sync(kComputeBarrier, 32 * NW);
     };
-    // rows y0 - 1 .. y0 + 2 of a tile's window take the four ring rows in turn
+    // consecutive rows take the four ring rows in turn; an iteration touches
+    // four consecutive rows (it reads q - 4 .. q - 2 and writes q - 1)
     auto rslot = [&](int y) -> float* { return pring + ((y - y0 + 1) & 3) * PC; };
     auto wslot = [&](int y) -> float* { return wring + ((y - y0 + 1) & 3) * PC; };
 
