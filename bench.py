@@ -244,8 +244,12 @@ def run_e2e(lbf, torch, steps, compact=False, tile=None):
     stats = lbf.Stats()
 
     def job():
-        d2h = 0
+        # every call below returns once its results are on the host (the
+        # steps run asynchronously until the next statistics read), so host
+        # clock readings between calls split the job without extra waits
+        d2h, marks = 0, [time.perf_counter()]
         lbf.lib().lb_init_phi(sim.h, 0, ctypes.c_void_p(phi0.data_ptr()), 0)
+        marks.append(time.perf_counter())
         done = 0
         while done < steps:
             k = min(100, steps - done)
@@ -253,20 +257,25 @@ def run_e2e(lbf, torch, steps, compact=False, tile=None):
             done += k
             lbf.lib().lb_moments(sim.h, 0, 0, None, None, None, None, ctypes.byref(stats))
             d2h += 48
+        marks.append(time.perf_counter())
         lbf.lib().lb_moments(sim.h, 0, 0, None, ctypes.c_void_p(out_phi.data_ptr()), None,
                              None, None)
-        return d2h
+        marks.append(time.perf_counter())
+        return d2h, marks
 
     job()  # warm-up: the step graphs are built on first use
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    d2h = job()
+    d2h, marks = job()
     dt = time.perf_counter() - t0
     d2h += out_phi.numel() * 8
     h2d = phi0.numel() * 8
     ok = bool(np.isfinite(out_phi.numpy()).all())
     sim.close()
-    return dict(seconds=dt, h2d=h2d, d2h=d2h, finite=ok)
+    split = [round((b - a) * 1e3, 2) for a, b in zip(marks, marks[1:])]
+    return dict(seconds=dt, h2d=h2d, d2h=d2h, finite=ok,
+                breakdown_ms={"upload_and_init": split[0], "steps_and_stats": split[1],
+                              "phi_readback": split[2]})
 
 
 def run_fp64(lbf, torch, steps, size=None, tile=None):
@@ -529,7 +538,8 @@ def ours(args):
                        "d2h_bytes_per_step": e2e["d2h"] // args.steps,
                        "job": "phi0 H2D from pinned memory, %d steps, stats D2H every 100 "
                               "steps, final phi D2H (after one untimed warm-up job that "
-                              "builds the step graphs)" % args.steps}
+                              "builds the step graphs)" % args.steps,
+                       "breakdown_ms": e2e["breakdown_ms"]}
         torch.cuda.empty_cache()
         extras = {}
         if compact:
