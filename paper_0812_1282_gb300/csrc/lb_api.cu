@@ -625,6 +625,26 @@ int check_geometry(const unsigned char* cls, int nx, int ny, int walls)
     return LB_OK;
 }
 
+// The device address of a page-locked host buffer (nullptr if the buffer is
+// pageable or not known to CUDA).
+double* device_alias(double* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // the query's error is not the caller's
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
+}
+
+// Are all requested host outputs page-locked (and so writable by a kernel)?
+bool host_mapped(double* const (&outs)[4])
+{
+    for (int k = 0; k < 4; ++k)
+        if (outs[k] && !device_alias(outs[k])) return false;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -691,10 +711,19 @@ int lb_init_phi(lb_handle* h, int dom, const double* phi0, int on_device)
     if (rc != LB_OK) return rc;
     if (!phi0) return fail(LB_ERR_INVALID_ARG, "phi0 is NULL");
     const DomDesc& D = h->descs[dom];
-    LB_CUDA(cudaMemcpy2DAsync(phi0_scratch(h, dom), sizeof(double) * D.pitch, phi0,
-                              sizeof(double) * D.nx, sizeof(double) * D.nx, D.ny,
-                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                              h->stream));
+    // page-locked host memory is read by a kernel through its device address
+    // (one pass over the host link); other host memory goes by copy
+    const double* alias = on_device ? nullptr : device_alias(const_cast<double*>(phi0));
+    if (alias) {
+        const int e = lbfe::launch_copy_rows(D, alias, phi0_scratch(h, dom), h->stream);
+        if (e != 0) return fail(LB_ERR_CUDA, "copy launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+        h->launches += 1;
+    } else {
+        LB_CUDA(cudaMemcpy2DAsync(phi0_scratch(h, dom), sizeof(double) * D.pitch, phi0,
+                                  sizeof(double) * D.nx, sizeof(double) * D.nx, D.ny,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream));
+    }
     rc = finish_init(h, dom);
     if (rc != LB_OK) return rc;
     LB_CUDA(cudaStreamSynchronize(h->stream));  // phi0 may be released by the caller
@@ -743,6 +772,15 @@ int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi, d
     if (any && on_device) {
         const int e = lbfe::launch_moments(h->precision, D, h->parity, 0, D.ny, rho, phi, ux, uy,
                                            D.nx, nullptr, 0, nullptr, h->stream);
+        if (e != 0) return fail(LB_ERR_CUDA, "moments launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+        h->launches += 1;
+    } else if (any && host_mapped(outs)) {
+        // page-locked host buffers are mapped into the device's address
+        // space: the kernel writes them directly, in one pass
+        double* dev[4];
+        for (int k = 0; k < 4; ++k) dev[k] = outs[k] ? device_alias(outs[k]) : nullptr;
+        const int e = lbfe::launch_moments(h->precision, D, h->parity, 0, D.ny, dev[0], dev[1],
+                                           dev[2], dev[3], D.nx, nullptr, 0, nullptr, h->stream);
         if (e != 0) return fail(LB_ERR_CUDA, "moments launch failed: %s", cudaGetErrorString(cudaError_t(e)));
         h->launches += 1;
     } else if (any) {

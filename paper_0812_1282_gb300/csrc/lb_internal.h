@@ -85,6 +85,8 @@ int launch_init_phi_random(int precision, const DomDesc& d, double* phi0, double
                            unsigned long long seed, void* stream);
 int launch_init_eq(int precision, const DomDesc& d, const double* phi0, int parity,
                    void* stream);
+// phi0 rows (nx per row, contiguous, device-addressable) into the pitched field.
+int launch_copy_rows(const DomDesc& d, const double* src, double* phi0, void* stream);
 int launch_moments(int precision, const DomDesc& d, int parity, int row0, int nrows,
                    double* rho, double* phi, double* ux, double* uy, long long ld,
                    double* partials, int max_partials, StatsOut* out, void* stream);

@@ -125,6 +125,27 @@ int launch_init_phi_drop(int, const DomDesc& d, double* phi0, double R, double c
     return static_cast<int>(cudaGetLastError());
 }
 
+// Rows of a caller's phi0 (nx per row, contiguous; page-locked host memory
+// seen through its device address) into the pitched scratch field.
+__global__ void copy_rows_kernel(const double* __restrict__ src, int nx, int ny,
+                                 double* __restrict__ dst, int pitch)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = int(k / nx), x = int(k - (long long)y * nx);
+        dst[(long long)y * pitch + x] = src[k];
+    }
+}
+
+int launch_copy_rows(const DomDesc& d, const double* src, double* phi0, void* stream)
+{
+    const long long n = (long long)d.nx * d.ny;
+    copy_rows_kernel<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        src, d.nx, d.ny, phi0, d.pitch);
+    return static_cast<int>(cudaGetLastError());
+}
+
 int launch_init_phi_random(int, const DomDesc& d, double* phi0, double amp,
                            unsigned long long seed, void* stream)
 {

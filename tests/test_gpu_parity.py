@@ -247,6 +247,59 @@ def test_stats_match_fields(lbf, orc):
     assert st["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("compact", [False, True])
+def test_host_outputs_pinned_and_pageable_agree(lbf, compact):
+    """Page-locked host outputs are written by the kernel directly, pageable
+    ones through the staging buffer: both receive the same fields."""
+    import ctypes
+
+    import torch
+
+    nx, ny = 301, 67
+    sim = lbf.Lattice(lbf.params(precision="fp32", compact_g=compact, collision="mrt",
+                                 tau_alpha=1.5, tau_beta=0.6), nx, ny)
+    sim.init_random(0.1, 99)
+    sim.step(25)
+    rho, phi, ux, uy, _ = sim.moments()
+    pinned = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    rc = lbf.lib().lb_moments(sim.h, 0, 0, *[ctypes.c_void_p(t.data_ptr()) for t in pinned],
+                              None)
+    assert rc == 0
+    for a, b in zip((rho, phi, ux, uy), pinned):
+        assert np.array_equal(a, b.numpy())
+    # a mix of page-locked and pageable outputs takes the staging path
+    mixed = np.empty((ny, nx))
+    rc = lbf.lib().lb_moments(sim.h, 0, 0, None, ctypes.c_void_p(pinned[1].data_ptr()),
+                              ctypes.c_void_p(mixed.ctypes.data), None, None)
+    assert rc == 0 and np.array_equal(mixed, ux) and np.array_equal(pinned[1].numpy(), phi)
+    sim.close()
+
+
+@pytest.mark.parametrize("compact", [False, True])
+def test_init_phi_pinned_and_pageable_agree(lbf, compact):
+    """A page-locked phi0 is read by a kernel, a pageable one is copied:
+    both give the same state."""
+    import ctypes
+
+    import torch
+
+    nx, ny = 203, 45
+    phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 11)
+    p = lbf.params(precision="fp32", compact_g=compact, collision="mrt", tau_alpha=1.5,
+                   tau_beta=0.6)
+    a = lbf.Lattice(p, nx, ny)
+    b = lbf.Lattice(p, nx, ny)
+    a.init_phi(phi0)
+    pinned = torch.from_numpy(phi0.copy()).pin_memory()
+    assert lbf.lib().lb_init_phi(b.h, 0, ctypes.c_void_p(pinned.data_ptr()), 0) == 0
+    assert a.save_state()[32:] == b.save_state()[32:]
+    a.step(10)
+    b.step(10)
+    assert a.save_state()[32:] == b.save_state()[32:]
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("theta", [45.0, 90.0, 135.0])
 def test_contact_angle_matches_oracle_fit(lbf, orc, theta):
     """lb_contact_angle (device crossings + host fit) against the oracle's
