@@ -142,7 +142,8 @@ int lb_init_drop(lb_handle* h, int dom, double R, double cx, double cy);
 int lb_init_random(lb_handle* h, int dom, double amp, unsigned long long seed);
 
 /* Arbitrary phi0: host (on_device = 0) or device (1) array [ny][nx] of
- * doubles, read before the call returns. */
+ * doubles, read before the call returns.  A page-locked host array is read
+ * by a kernel through its device address; pageable host memory is copied. */
 int lb_init_phi(lb_handle* h, int dom, const double* phi0, int on_device);
 
 /* Advance every domain of the handle by n >= 0 time steps (Steps 1-4 of
@@ -151,7 +152,9 @@ int lb_init_phi(lb_handle* h, int dom, const double* phi0, int on_device);
 int lb_step(lb_handle* h, int n);
 
 /* Moments of domain dom.  rho, phi, ux, uy: [ny][nx] double buffers on the
- * host (on_device = 0) or the device (1); any may be NULL.  stats may be
+ * host (on_device = 0) or the device (1); any may be NULL.  When every
+ * requested host buffer is page-locked the kernel writes them directly;
+ * otherwise they are filled through a device staging buffer.  stats may be
  * NULL.  Synchronises the stream.  Returns LB_ERR_NONFINITE (after filling
  * the outputs) if a node's moments are not finite. */
 int lb_moments(lb_handle* h, int dom, int on_device, double* rho, double* phi,
