@@ -453,10 +453,31 @@ def cpu_baseline(seconds=12.0):
         lat.step(5)
         done += 5
     dt = time.perf_counter() - t0
-    return {"value": n * n * done / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(),
-            "kind": "oracle",
-            "sample": "%dx%d cut of the 8192^2 spinodal MRT workload, %d FP64 steps (%.1f s)"
-                      % (n, n, done, dt)}
+    res = {"value": n * n * done / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(),
+           "kind": "oracle",
+           "sample": "%dx%d cut of the 8192^2 spinodal MRT workload, %d FP64 steps (%.1f s)"
+                     % (n, n, done, dt)}
+    # the same cut on one core, and the 100 x 50 BGK drop on all cores
+    # (about 3 s each)
+    threads = oracle.get_threads()
+
+    def rate(lattice, nodes, budget):
+        k, t1 = 0, time.perf_counter()
+        while time.perf_counter() - t1 < budget:
+            lattice.step(5)
+            k += 5
+        return nodes * k / (time.perf_counter() - t1) / 1e6
+
+    try:
+        oracle.set_threads(1)
+        res["single_core_mlups"] = round(rate(lat, n * n, 3.0), 3)
+    finally:
+        oracle.set_threads(threads)
+    d = lbinputs.DROP_100x50
+    small = oracle.OracleLattice(oracle.params(**d["params"]), d["nx"], d["ny"])
+    small.init_drop(d["R"], d["cx"], d["cy"])
+    res["drop_100x50_mlups"] = round(rate(small, d["nx"] * d["ny"], 3.0), 3)
+    return res
 
 
 def ours(args):
