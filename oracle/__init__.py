@@ -63,13 +63,14 @@ class OrcParams(ctypes.Structure):
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("walls", ctypes.c_int), ("mrt_all_rates", ctypes.c_int),
         ("step2_relax_momentum", ctypes.c_int), ("mrt_lut", ctypes.c_int),
+        ("wetting_rule", ctypes.c_int),
     ]
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
            tau_beta=1.0, h_bottom=0.0, h_top=0.0, collision="bgk",
            zero_u_at_walls=None, walls=True, mrt_all_rates=False,
-           step2_relax_momentum=False, mrt_lut=0) -> OrcParams:
+           step2_relax_momentum=False, mrt_lut=0, wetting_rule=0) -> OrcParams:
     """Parameter block.  ``zero_u_at_walls`` defaults to on for MRT (the
     proposed algorithm of Sec. V) and off for BGK."""
     coll = {"bgk": 0, "mrt": 1}[collision] if isinstance(collision, str) else int(collision)
@@ -77,7 +78,8 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0,
         zero_u_at_walls = coll == 1
     return OrcParams(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom,
                      h_top, coll, int(bool(zero_u_at_walls)), int(bool(walls)),
-                     int(bool(mrt_all_rates)), int(bool(step2_relax_momentum)), int(mrt_lut))
+                     int(bool(mrt_all_rates)), int(bool(step2_relax_momentum)), int(mrt_lut),
+                     int(wetting_rule))
 
 
 _D = ctypes.POINTER(ctypes.c_double)

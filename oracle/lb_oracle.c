@@ -33,7 +33,8 @@
  *    (xi = kappa*h, Sec. II); a ghost row mirrors phi about the boundary row:
  *    phi(x,-1) = phi(x,1) - 2 h_bottom, phi(x,ny) = phi(x,ny-2) - 2 h_top,
  *    which makes the isotropic y-derivative at the boundary row equal to the
- *    imposed inward gradient exactly;
+ *    imposed inward gradient exactly (with wetting_rule = 1 instead the
+ *    one-sided difference across the wall plane: phi(x,-1) = phi(x,0) - h);
  *  - boundary nodes of Step 2 are the fluid rows adjacent to a wall;
  *  - conserved-moment rates are the literal zeros of Eq. diag (optionally,
  *    step2_relax_momentum: rate 1 for the momentum rows on Step-2 nodes).
@@ -62,7 +63,14 @@ typedef struct orc_params {
                                  nodes (default 0: the literal zeros of Eq. diag) */
     int mrt_lut;              /* MRT: 0 = exact tau(phi); n >= 2 = the nearest of n
                                  tabulated viscosities (Sec. V lookup table)  */
+    int wetting_rule;         /* ghost of the wetting condition (Sec. II): 0 = mirror
+                                 about the boundary row, phi(-1) = phi(1) - 2h; 1 =
+                                 one-sided at the wall plane, phi(-1) = phi(0) - h */
 } orc_params;
+
+/* Mirror distance of the wetting ghost: 2 (about the boundary row) or 1
+ * (one-sided difference across the wall plane). */
+static int wet_k(const orc_params* p) { return p->wetting_rule ? 1 : 2; }
 
 /* ---------------------------------------------------------------- lattice */
 static const int EX[9] = {0, 1, -1, 0, 0, 1, -1, -1, 1};
@@ -232,8 +240,9 @@ static double phi_at(const orc_params* p, int nx, int ny, const double* phi,
 {
     x = wrap(x, nx);
     if (!p->walls) return phi[(size_t)wrap(y, ny) * nx + x];
-    if (y < 0) return phi[(size_t)1 * nx + x] - 2.0 * p->h_bottom;
-    if (y >= ny) return phi[(size_t)(ny - 2) * nx + x] - 2.0 * p->h_top;
+    const int k = wet_k(p);
+    if (y < 0) return phi[(size_t)(k - 1) * nx + x] - k * p->h_bottom;
+    if (y >= ny) return phi[(size_t)(ny - k) * nx + x] - k * p->h_top;
     return phi[(size_t)y * nx + x];
 }
 
@@ -527,9 +536,11 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
                     const int qy = y + r - 1;
                     double v;
                     if (p->walls && qy < 0)
-                        v = phi_full[(size_t)(1 - ry0) * nx + qx] - 2.0 * p->h_bottom;
+                        v = phi_full[(size_t)(wet_k(p) - 1 - ry0) * nx + qx] -
+                            wet_k(p) * p->h_bottom;
                     else if (p->walls && qy >= ny)
-                        v = phi_full[(size_t)(ny - 2 - ry0) * nx + qx] - 2.0 * p->h_top;
+                        v = phi_full[(size_t)(ny - wet_k(p) - ry0) * nx + qx] -
+                            wet_k(p) * p->h_top;
                     else
                         v = phi_full[(size_t)(qy - ry0) * nx + qx];
                     sx += DX_STENCIL[r][c] * v;
@@ -585,7 +596,8 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
  *    neighbours;
  *  - wetting ghost value of a solid node s next to fluid: the mirror rule of
  *    the flat wall applied along each axis direction d in which s + d is
- *    fluid, averaged: phi(s) = mean_d phi(s + 2d) - 2 h(s).  If no axis
+ *    fluid, averaged: phi(s) = mean_d phi(s + 2d) - 2 h(s) (one-sided rule:
+ *    mean_d phi(s + d) - h(s)).  If no axis
  *    neighbour is fluid (s touches fluid through a corner only) the
  *    diagonal directions are used the same way.  Every mirror node s + 2d
  *    must be fluid (features at least two nodes thick); otherwise the
@@ -659,11 +671,12 @@ static double geo_phi_at(const orc_params* p, int nx, int ny, const unsigned cha
     int dirs[4][2];
     const int n = geo_mirror_dirs(p, nx, ny, cls, x, y, dirs);
     double sum = 0.0;
+    const int m = wet_k(p);
     for (int k = 0; k < n; ++k) {
-        const int mx = x + 2 * dirs[k][0], my = y + 2 * dirs[k][1];
+        const int mx = x + m * dirs[k][0], my = y + m * dirs[k][1];
         sum += phi[(size_t)wrap(my, ny) * nx + wrap(mx, nx)];
     }
-    return sum / n - 2.0 * geo_h(p, nx, ny, cls, hcls, x, y);
+    return sum / n - m * geo_h(p, nx, ny, cls, hcls, x, y);
 }
 
 /* Eq. best at every fluid node with the ghost rule at solid neighbours;

@@ -282,6 +282,39 @@ def test_wetting_ghost_rows_impose_the_gradient(oracle_mod):
     assert np.allclose(dy[-1], -p.h_top, atol=1e-15)
 
 
+def test_one_sided_wetting_rule_sets_the_wall_plane_difference(oracle_mod):
+    """The alternative discretisation of the wetting condition (reading 2):
+    the ghost row takes phi(x,-1) = phi(x,0) - h, so the one-sided
+    difference across the wall plane y = -1/2 equals h.  On a field linear
+    in y (slope g) the isotropic y-gradient of the boundary row is then
+    (g + h)/2 at the bottom and (g - h_top)/2 at the top; the mirror rule
+    would give h and -h_top."""
+    g = 0.037
+    p = oracle_mod.params(h_bottom=-0.2368, h_top=0.1234, wetting_rule=1)
+    y = np.arange(9, dtype=float)[:, None]
+    phi = 0.3 + g * y + 0.0 * np.arange(13)[None, :]
+    _, dy, _ = oracle_mod.phi_derivatives(p, phi)
+    assert np.allclose(dy[0], 0.5 * (g + p.h_bottom), atol=1e-15)
+    assert np.allclose(dy[-1], 0.5 * (g - p.h_top), atol=1e-15)
+    assert np.allclose(dy[1:-1], g, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_one_sided_wetting_rule_drop_angle(oracle_mod, theta):
+    """With the one-sided ghost the sessile drop also settles near Eq.
+    (theory): 60 -> 57.3 and 120 -> 121.9 degrees on this 2.8-node-wide
+    interface after 9000 steps (the mirror rule gives 58.2 and 123.8)."""
+    nx, ny, R = 120, 60, 25.0
+    p = oracle_mod.params(tau_alpha=1.0, tau_beta=1.0, h_bottom=oracle_mod.wetting_h(theta),
+                          h_top=0.0, gamma_mob=0.5, wetting_rule=1)
+    lat = oracle_mod.OracleLattice(p, nx, ny)
+    lat.init_drop(R, nx / 2, -0.5)
+    lat.step(9000)
+    _, ph, _, _ = lat.moments()
+    th, *_ = oracle_mod.contact_angle(ph)
+    assert th == pytest.approx(theta, abs=4.5)
+
+
 # ------------------------------------------------- contact-angle theory
 def _young_cos_theta(h, a, kappa):
     """cos(theta) from Young's law (Eq. Young) with Cahn wall tensions: the
