@@ -84,6 +84,14 @@ typedef struct lb_params {
                             scheme is the same; g'_0 = phi - sum g'_i is implicit.
                             lb_set_populations is not available on such a handle.
                             Default 0. */
+    int wetting_rule;    /* discretisation of the wetting condition of Sec. II (the
+                            inward normal derivative of phi at a wall equals h): 0
+                            (default) mirrors phi about the boundary row, ghost
+                            phi(x,-1) = phi(x,1) - 2 h, so the isotropic gradient of the
+                            boundary row is h; 1 takes the one-sided difference across
+                            the wall plane, phi(x,-1) = phi(x,0) - h.  At obstacles the
+                            same rule along each direction towards the fluid
+                            (phi(s) = mean phi(s + 2d) - 2h, or mean phi(s + d) - h). */
 } lb_params;
 
 /* Diagnostics of one domain (sums over all nodes, in FP64). */

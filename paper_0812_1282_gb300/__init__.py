@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
         ("collision", ctypes.c_int), ("zero_u_at_walls", ctypes.c_int),
         ("precision", ctypes.c_int), ("walls", ctypes.c_int),
         ("step2_relax_momentum", ctypes.c_int), ("mrt_lut", ctypes.c_int),
-        ("compact_g", ctypes.c_int),
+        ("compact_g", ctypes.c_int), ("wetting_rule", ctypes.c_int),
     ]
 
 
@@ -76,7 +76,7 @@ class Stats(ctypes.Structure):
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,
            h_bottom=0.0, h_top=0.0, collision="bgk", zero_u_at_walls=None,
            precision="fp64", walls=True, step2_relax_momentum=False, mrt_lut=0,
-           compact_g=False) -> Params:
+           compact_g=False, wetting_rule=0) -> Params:
     """Parameter block (lattice units).  Step 2 of the proposed algorithm
     (zero equilibrium velocity on wall rows) defaults to on for MRT and off
     for BGK; step2_relax_momentum selects the alternative reading of the
@@ -87,7 +87,8 @@ def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_be
         zero_u_at_walls = coll == LB_MRT
     return Params(a, kappa, gamma_mob, tau_phi, tau_alpha, tau_beta, h_bottom, h_top, coll,
                   int(bool(zero_u_at_walls)), prec, int(bool(walls)),
-                  int(bool(step2_relax_momentum)), int(mrt_lut), int(bool(compact_g)))
+                  int(bool(step2_relax_momentum)), int(mrt_lut), int(bool(compact_g)),
+                  int(wetting_rule))
 
 
 _lib = None

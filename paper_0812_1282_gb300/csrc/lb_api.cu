@@ -162,6 +162,8 @@ int validate(const lb_params* p)
         return fail(LB_ERR_INVALID_ARG, "compact_g must be 0 or 1");
     if (p->compact_g && (p->precision != LB_FP32 || p->tau_phi != 1.0))
         return fail(LB_ERR_INVALID_ARG, "compact_g needs LB_FP32 and tau_phi = 1");
+    if (p->wetting_rule != 0 && p->wetting_rule != 1)
+        return fail(LB_ERR_INVALID_ARG, "wetting_rule must be 0 or 1");
     return LB_OK;
 }
 
@@ -460,6 +462,7 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.step2 = p.zero_u_at_walls ? 1 : 0;
         D.step2_relax_j = p.step2_relax_momentum ? 1 : 0;
         D.compact = p.compact_g ? 1 : 0;
+        D.wet_k = p.wetting_rule ? 1 : 2;
         D.a = p.a;
         D.kappa = p.kappa;
         D.gamma = p.gamma_mob;

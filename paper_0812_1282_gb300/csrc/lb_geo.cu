@@ -7,9 +7,10 @@
 //   - Step 2 (zero equilibrium velocity) applies to fluid nodes with a solid
 //     node among their eight neighbours;
 //   - a solid node s next to fluid carries the wetting ghost value: the
-//     flat-wall mirror phi(s + 2d) - 2 h(s), averaged over the axis
-//     directions d whose neighbour s + d is fluid, or over the diagonal
-//     directions if s touches fluid only through a corner.  The host rejects
+//     flat-wall mirror phi(s + 2d) - 2 h(s) (or, with the one-sided rule,
+//     phi(s + d) - h(s)), averaged over the axis directions d whose
+//     neighbour s + d is fluid, or over the diagonal directions if s
+//     touches fluid only through a corner.  The host rejects
 //     maps where a mirror node s + 2d is solid (features thinner than two
 //     nodes).  On an obstacle-free lattice this is the ghost-row rule of the
 //     plain step, so both paths agree there.
@@ -120,7 +121,7 @@ __device__ Real ghost_phi(const DomDesc& D, const GeoView& G, const Real* phi, i
         const int dx = j == 0 ? 1 : (j == 1 ? -1 : 0);
         const int dy = j == 2 ? 1 : (j == 3 ? -1 : 0);
         if (!G.solid(x + dx, y + dy)) {
-            sum += phi_field(phi, G, x + 2 * dx, y + 2 * dy);
+            sum += phi_field(phi, G, x + D.wet_k * dx, y + D.wet_k * dy);
             ++n;
         }
     }
@@ -131,13 +132,13 @@ __device__ Real ghost_phi(const DomDesc& D, const GeoView& G, const Real* phi, i
             const int dx = (j == 0 || j == 3) ? 1 : -1;
             const int dy = (j == 0 || j == 2) ? 1 : -1;
             if (!G.solid(x + dx, y + dy)) {
-                sum += phi_field(phi, G, x + 2 * dx, y + 2 * dy);
+                sum += phi_field(phi, G, x + D.wet_k * dx, y + D.wet_k * dy);
                 ++n;
             }
         }
     }
     const Real mean = n == 1 ? sum : (n == 2 ? sum * Real(0.5) : (n == 3 ? div_const<3>(sum) : sum * Real(0.25)));
-    return mean - Real(2) * h;
+    return mean - Real(D.wet_k) * h;
 }
 
 // The nine pulled values of fluid node (x, y) from population set `src`
@@ -248,7 +249,7 @@ __global__ void geo_init_eq_kernel(DomDesc D, const double* __restrict__ phi0, i
                 const int ddx = j == 0 ? 1 : (j == 1 ? -1 : 0);
                 const int ddy = j == 2 ? 1 : (j == 3 ? -1 : 0);
                 if (!G.solid(qx + ddx, qy + ddy)) {
-                    sum += at(qx + 2 * ddx, qy + 2 * ddy);
+                    sum += at(qx + D.wet_k * ddx, qy + D.wet_k * ddy);
                     ++n;
                 }
             }
@@ -257,12 +258,12 @@ __global__ void geo_init_eq_kernel(DomDesc D, const double* __restrict__ phi0, i
                     const int ddx = (j == 0 || j == 3) ? 1 : -1;
                     const int ddy = (j == 0 || j == 2) ? 1 : -1;
                     if (!G.solid(qx + ddx, qy + ddy)) {
-                        sum += at(qx + 2 * ddx, qy + 2 * ddy);
+                        sum += at(qx + D.wet_k * ddx, qy + D.wet_k * ddy);
                         ++n;
                     }
                 }
             const double mean = n == 1 ? sum : (n == 2 ? sum * 0.5 : (n == 3 ? div_const<3>(sum) : sum * 0.25));
-            return mean - 2.0 * h;
+            return mean - D.wet_k * h;
         };
         double nb[9];
         for (int i = 1; i < 9; ++i) {

@@ -33,6 +33,9 @@ struct DomDesc {
     int step2_relax_j; // MRT: relax wall-row momentum at rate 1 (alternative reading)
     int compact;       // FP32, tau_phi = 1: g stored as (phi word, Gamma mu, u_eq) in
                        // g planes 0..3 (lb_step_compact.cuh)
+    int wet_k;         // wetting ghost: phi(ghost) = phi(k - 1 rows inside) - k h, with
+                       // k = 2 (mirror about the boundary row) or 1 (one-sided across
+                       // the wall plane); at obstacles mean phi(s + k d) - k h
     double a, kappa, gamma;   // free energy and mobility parameters
     double omega_phi;         // 1 / tau_phi
     double tau_c0, tau_c1;    // tau_rho(phi) = tau_c0 + tau_c1 * phi  (Eq. tau)

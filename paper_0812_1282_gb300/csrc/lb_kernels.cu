@@ -187,9 +187,9 @@ __global__ void init_eq_kernel(DomDesc D, const double* __restrict__ phi0, int p
             for (int c = 0; c < 3; ++c) {
                 double val;
                 if (D.walls && yy < 0)
-                    val = phi0[(long long)1 * pitch + cols[c]] - 2.0 * D.h_bot;
+                    val = phi0[(long long)(D.wet_k - 1) * pitch + cols[c]] - D.wet_k * D.h_bot;
                 else if (D.walls && yy >= ny)
-                    val = phi0[(long long)(ny - 2) * pitch + cols[c]] - 2.0 * D.h_top;
+                    val = phi0[(long long)(ny - D.wet_k) * pitch + cols[c]] - D.wet_k * D.h_top;
                 else {
                     const int yw = yy < 0 ? ny - 1 : (yy >= ny ? 0 : yy);
                     val = phi0[(long long)yw * pitch + cols[c]];

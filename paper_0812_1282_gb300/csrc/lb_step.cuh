@@ -268,7 +268,9 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
         wait_full(1);
         if (active) {
             publish(1, 1, 1);
-            ghost_row(-1, 1, Real(2) * prm.h_bot);  // each lane mirrors its own entries
+            // each lane forms its own entries: row k - 1 less k h (k = 2:
+            // mirror about row 0; k = 1: one-sided across the wall plane)
+            ghost_row(-1, D.wet_k - 1, Real(D.wet_k) * prm.h_bot);
         }
     }
     bool have_next = bottom_ghost;
@@ -279,7 +281,7 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
                 wait_full(yn - first);
                 if (active) publish(yn - first, wrap_row(yn), yn);
             } else if (active) {
-                ghost_row(yn, ny - 2, Real(2) * prm.h_top);
+                ghost_row(yn, ny - D.wet_k, Real(D.wet_k) * prm.h_top);
             }
         }
         have_next = false;

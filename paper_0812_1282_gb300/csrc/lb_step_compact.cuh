@@ -251,7 +251,6 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     f2 u_next = zero;                 // U(q + 1)
     f2 uh = zero, wd = zero, tl = zero;  // U + H, phi word, tail of row q - 1
     f2 d_wall = zero;                 // D of the top wall row, from that row itself
-    const float h2b = 2.f * prm.h_bot, h2t = 2.f * prm.h_top;
     const unsigned kAll = 0xffffffffu;
     for (int p = 0; p < T.count(); ++p) {
         const int qr = T.clo + p;  // compact row of this stage
@@ -322,8 +321,8 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             fi[7] = blo ? ld_pair(sb + 7 * segw) : ld_two(sb + 7 * segw + 1);
             fi[8] = bhi ? ld_pair(sb + 8 * segw) : ld_two(sb + 8 * segw - 1);
             // phi of strip columns jn + 1 .. jn + 4 of rows y - 1, y, y + 1
-            // (centres jn + 2, jn + 3); the wall ghost rows mirror rows 1 and
-            // ny - 2 less 2h
+            // (centres jn + 2, jn + 3); a wall ghost row is row k - 1 (or
+            // ny - k) less k h: the mirror (k = 2) or one-sided (k = 1) rule
             auto row3 = [&](const float* rw, f2& w, f2& c, f2& e) {
                 const float2 a = ld_pair(rw + jn), b = ld_pair(rw + jn + 2),
                              d = ld_pair(rw + jn + 4);
@@ -334,8 +333,8 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             f2 cw_, cc, ce, nw_, nc, ne, sw, sc_, se;
             row3(rslot(y), cw_, cc, ce);
             if (bhi) {
-                row3(rslot(ny - 2), nw_, nc, ne);
-                const f2 h(h2t);
+                row3(rslot(ny - D.wet_k), nw_, nc, ne);
+                const f2 h(float(D.wet_k) * prm.h_top);
                 nw_ = nw_ - h;
                 nc = nc - h;
                 ne = ne - h;
@@ -343,8 +342,8 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
                 row3(rslot(y + 1), nw_, nc, ne);
             }
             if (blo) {
-                row3(rslot(1), sw, sc_, se);
-                const f2 h(h2b);
+                row3(rslot(D.wet_k - 1), sw, sc_, se);
+                const f2 h(float(D.wet_k) * prm.h_bot);
                 sw = sw - h;
                 sc_ = sc_ - h;
                 se = se - h;

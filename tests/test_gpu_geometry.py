@@ -48,15 +48,18 @@ def max_diff(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max())
 
 
-def _kw(orc, coll, relax=False):
+def _kw(orc, coll, relax=False, rule=0):
     return dict(collision=coll, tau_alpha=1.4, tau_beta=0.7, h_bottom=orc.wetting_h(65.0),
-                h_top=orc.wetting_h(115.0), gamma_mob=0.3, step2_relax_momentum=relax)
+                h_top=orc.wetting_h(115.0), gamma_mob=0.3, step2_relax_momentum=relax,
+                wetting_rule=rule)
 
 
-@pytest.mark.parametrize("coll,relax", [("bgk", False), ("mrt", False), ("mrt", True)])
-def test_fp64_blocks_match_oracle(lbf, orc, coll, relax):
+@pytest.mark.parametrize("coll,relax,rule", [("bgk", False, 0), ("mrt", False, 0),
+                                             ("mrt", True, 0), ("mrt", False, 1),
+                                             ("bgk", False, 1)])
+def test_fp64_blocks_match_oracle(lbf, orc, coll, relax, rule):
     nx, ny = 40, 24
-    kw = _kw(orc, coll, relax)
+    kw = _kw(orc, coll, relax, rule)
     cls = blocks_geometry(nx, ny)
     hc = [0.0, orc.wetting_h(50.0), orc.wetting_h(130.0), 0.1]
     phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 14)
@@ -141,14 +144,15 @@ def test_fp32_channel_within_1e5_after_1000_steps(lbf, orc):
     sim.close()
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
-def test_obstacle_free_map_equals_plain_kernel(lbf, orc, prec, tol):
+def test_obstacle_free_map_equals_plain_kernel(lbf, orc, prec, tol, rule):
     """The obstacle kernels on an all-fluid map and the staged plain kernel
     compute the same arithmetic (the compiler may contract products into
     fused multiply-adds differently in the two kernels, so agreement is to
     rounding, not bitwise)."""
     nx, ny = 70, 33
-    kw = dict(_kw(orc, "mrt"), precision=prec)
+    kw = dict(_kw(orc, "mrt", rule=rule), precision=prec)
     phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 21)
     a = lbf.Lattice(lbf.params(**kw), nx, ny)
     b = lbf.Lattice(lbf.params(**kw), nx, ny)

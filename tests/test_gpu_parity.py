@@ -247,6 +247,30 @@ def test_stats_match_fields(lbf, orc):
     assert st["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp32c"])
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+def test_one_sided_wetting_rule_matches_oracle(lbf, orc, coll, storage):
+    """The alternative wetting discretisation (ghost phi(x,-1) = phi(x,0) -
+    h, the one-sided difference across the wall plane) against the oracle:
+    FP64 to 1e-12, FP32 (full and compact g storage) to 1e-5."""
+    nx, ny, steps = 97, 41, 600
+    kw = dict(collision=coll, tau_alpha=1.5, tau_beta=0.6, h_bottom=orc.wetting_h(60.0),
+              h_top=orc.wetting_h(110.0), wetting_rule=1)
+    sim = lbf.Lattice(lbf.params(precision="fp64" if storage == "fp64" else "fp32",
+                                 compact_g=storage == "fp32c", **kw), nx, ny)
+    ref = orc.OracleLattice(orc.params(**kw), nx, ny)
+    for s in (sim, ref):
+        s.init_drop(15.0, 48.0, -0.5)
+        s.step(steps)
+    _, phi, ux, uy, st = sim.moments()
+    _, rphi, rux, ruy = ref.moments()
+    tol = 1e-12 if storage == "fp64" else 1e-5
+    assert np.abs(phi - rphi).max() <= tol
+    assert max(np.abs(ux - rux).max(), np.abs(uy - ruy).max()) <= tol
+    assert st["nonfinite"] == 0
+    sim.close()
+
+
 @pytest.mark.parametrize("compact", [False, True])
 def test_host_outputs_pinned_and_pageable_agree(lbf, compact):
     """Page-locked host outputs are written by the kernel directly, pageable
@@ -385,6 +409,8 @@ def test_invalid_arguments(lbf):
     assert e.value.code == lbf.LB_ERR_INVALID_ARG
     with pytest.raises(lbf.LBError):
         lbf.Lattice(lbf.params(), 2, 16)
+    with pytest.raises(lbf.LBError):
+        lbf.Lattice(lbf.params(wetting_rule=2), 16, 16)
     sim = lbf.Lattice(lbf.params(), 16, 16)
     with pytest.raises(lbf.LBError):
         sim.set_tile(48, 4)
