@@ -112,11 +112,13 @@ def test_compact_ragged_sizes_and_tile_independence(lbf, orc, nx, ny, walls):
     assert all(o == outs[0] for o in outs[1:])
 
 
-def test_compact_batch_is_bitwise_equal_to_single_domains(lbf):
+@pytest.mark.parametrize("walls,rule", [(True, 0), (False, 0), (True, 1)])
+def test_compact_batch_is_bitwise_equal_to_single_domains(lbf, walls, rule):
     specs = lbinputs.batch_specs(n=12, seed=7, lo=40, hi=200)
     plist = [lbf.params(**lbinputs.BASE, collision="mrt", precision="fp32", compact_g=True,
-                        tau_alpha=s["tau_alpha"], tau_beta=s["tau_beta"],
-                        h_bottom=lbf.lb_wetting_h(s["theta"])) for s in specs]
+                        tau_alpha=s["tau_alpha"], tau_beta=s["tau_beta"], walls=walls,
+                        h_bottom=lbf.lb_wetting_h(s["theta"]), wetting_rule=rule)
+             for s in specs]
     batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
     batch.set_tile(128, 8)
     for d, s in enumerate(specs):
