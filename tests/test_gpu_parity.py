@@ -469,13 +469,15 @@ def test_lookup_table_mrt_matches_oracle(lbf, orc, n):
     f, g = sim.populations()
     assert max_diff(f, ref.f) <= 1e-12 and max_diff(g, ref.g) <= 1e-12
     sim.close()
-    sim, ref = make_pair(lbf, orc, 96, 40, "fp32", **kw)
-    sim.init_drop(18.0, 48.0, -0.5)
+    ref = orc.OracleLattice(orc.params(**kw), 96, 40)
     ref.init_drop(18.0, 48.0, -0.5)
-    sim.step(1000)
     ref.step(1000)
-    _, phi, ux, uy, _ = sim.moments()
     _, rphi, rux, ruy = ref.moments()
-    assert max_diff(phi, rphi) <= 1e-5
-    assert max_diff(ux, rux) <= 1e-5 and max_diff(uy, ruy) <= 1e-5
-    sim.close()
+    for compact in (False, True):  # full and compact g storage
+        sim = lbf.Lattice(lbf.params(precision="fp32", compact_g=compact, **kw), 96, 40)
+        sim.init_drop(18.0, 48.0, -0.5)
+        sim.step(1000)
+        _, phi, ux, uy, _ = sim.moments()
+        assert max_diff(phi, rphi) <= 1e-5, compact
+        assert max_diff(ux, rux) <= 1e-5 and max_diff(uy, ruy) <= 1e-5, compact
+        sim.close()
