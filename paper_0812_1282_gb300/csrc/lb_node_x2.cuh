@@ -79,7 +79,8 @@ __device__ __forceinline__ void stencils2(f2 c, f2 e, f2 w, f2 n, f2 s, f2 ne, f
 }
 
 // Appendix A equilibria for i = 1..8 in deviation form (f_equilibria)
-__device__ __forceinline__ void f_equilibria2(const NodeParams<float>& P, f2 drho, f2 phi, f2 jxe,
+template <class PP>
+__device__ __forceinline__ void f_equilibria2(PP& P, f2 drho, f2 phi, f2 jxe,
                                               f2 jye, f2 uxe, f2 uye, f2 dx, f2 dy, f2 lap,
                                               f2 (&fe)[9], f2& m7eq, f2& m8eq)
 {
@@ -112,7 +113,8 @@ __device__ __forceinline__ void f_equilibria2(const NodeParams<float>& P, f2 drh
 }
 
 // Gamma mu, Eq. (chempot)
-__device__ __forceinline__ f2 gamma_mu2(const NodeParams<float>& P, f2 phi, f2 lap)
+template <class PP>
+__device__ __forceinline__ f2 gamma_mu2(PP& P, f2 phi, f2 lap)
 {
     const f2 mu = fma2(-P.kappa, lap, P.a * fma2(phi * phi, phi, f2(0.f) - phi));
     return P.gamma * mu;
@@ -147,8 +149,8 @@ __device__ __forceinline__ f2 g_tail_sum2(const f2 (&g)[9])
 
 // The f part of Steps 1-3 (collide_f) for two nodes of one row.  step2 and
 // step2_relax_j are those of the row.
-template <bool MRT>
-__device__ __forceinline__ void collide_f2(const NodeParams<float>& P, const f2 (&f)[9], f2 phi,
+template <bool MRT, class PP>
+__device__ __forceinline__ void collide_f2(PP& P, const f2 (&f)[9], f2 phi,
                                            f2 dx, f2 dy, f2 lap, bool step2, bool step2_relax_j,
                                            f2 (&fo)[9], f2& uxe_out, f2& uye_out)
 {

@@ -194,7 +194,8 @@ __device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
-                                               int nw, int cw, unsigned& q)
+                                               int nw, int cw, unsigned& q,
+                                               const NodeParams<float>* prm_shared = nullptr)
 {
     const int NW = NWC > 0 ? NWC : nw;
     float* __restrict__ fd = static_cast<float*>(parity ? D.f[0] : D.f[1]);
@@ -353,9 +354,16 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             f2 dx, dy, lap;
             stencils2(cc, ce, cw_, nc, sc_, ne, nw_, se, sw, dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
-            f2 fo2[9], uxe, uye;
-            collide_f2<MRT>(prm, fi, cc, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
-            const f2 co2[4] = {f2(ld_pair(wslot(y) + jn + 2)), gamma_mu2(prm, cc, lap), uxe, uye};
+            f2 fo2[9], uxe, uye, gmu;
+            if (prm_shared) {
+                const volatile NodeParams<float>& PV = *prm_shared;
+                collide_f2<MRT>(PV, fi, cc, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
+                gmu = gamma_mu2(PV, cc, lap);
+            } else {
+                collide_f2<MRT>(prm, fi, cc, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
+                gmu = gamma_mu2(prm, cc, lap);
+            }
+            const f2 co2[4] = {f2(ld_pair(wslot(y) + jn + 2)), gmu, uxe, uye};
             const int o = y * pitch + x + kXOff;  // even: pairs are 8-byte aligned
             if (jn + 1 < ncols) {
 #pragma unroll

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int tags[kStagesC];
+    __shared__ NodeParams<float> tile_prm;  // the current tile's node parameters
     constexpr int S = kStagesC;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages_c<S>(smem, NW);
@@ -155,8 +156,12 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
             if (named_sync_or(kComputeBarrier, 32 * NW, it < 0 || it >= n_items)) break;
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
+            // every compute warp is past the previous tile: refresh the shared
+            // copy of the node parameters, which the collision reads at each use
+            if (warp == 1 && lane == 0) tile_prm = node_params<float>(D);
+            named_sync(kComputeBarrier, 32 * NW);
             consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, w.cols, smem, NW,
-                                        warp - 1, q);
+                                        warp - 1, q, &tile_prm);
         }
     }
 }
