@@ -41,6 +41,9 @@ __device__ __forceinline__ f2 fma2(float k, f2 b, f2 c)
     return f2(__ffma2_rn(make_float2(k, k), b.v, c.v));
 }
 
+// The node parameters P of the functions below are a NodeParams<float> or a
+// volatile one (in shared memory, read at each use).
+
 // x / K, unbiased (the residual step of div_const<K, float>)
 template <int K>
 __device__ __forceinline__ f2 div_const2(f2 x)

@@ -190,7 +190,9 @@ __device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<
 // Compute warp cw of NW.  Its lane expands columns je, je + 1 (je = 62 cw +
 // 2 lane; strip column j is lattice column x0 - 2 + j) and collides nodes
 // jn, jn + 1 (jn = 2 (32 cw + lane); node n is lattice column x0 + n).  The
-// phi and word rings are indexed by strip column j.
+// phi and word rings are indexed by strip column j.  prm_shared, when set,
+// holds the node parameters in shared memory; the collision then reads them
+// at each use instead of keeping them in registers for the whole tile.
 template <bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
