@@ -19,6 +19,8 @@
 
 namespace lbfe {
 
+// The node functions below take their parameters P as a NodeParams<Real>
+// or as a volatile one (in shared memory, read at each use).
 template <typename Real>
 struct NodeParams {
     Real a, kappa, gamma, omega_phi, tau_c0, tau_c1, h_bot, h_top;
@@ -165,8 +167,8 @@ __device__ __forceinline__ void stencils<double>(double c, double e, double w, d
 // m7eq / m8eq receive the two stress moments of f^eq (rows 7, 8 of Eq.
 // Matrix): (fe1 + fe2) - (fe3 + fe4) = rho(ux^2 - uy^2) + kappa(dx^2 - dy^2) and
 // (fe5 + fe6) - (fe7 + fe8) = rho ux uy + kappa dx dy.
-template <typename Real>
-__device__ __forceinline__ void f_equilibria(const NodeParams<Real>& P, Real drho, Real phi,
+template <typename Real, class PP>
+__device__ __forceinline__ void f_equilibria(PP& P, Real drho, Real phi,
                                              Real jxe, Real jye, Real uxe, Real uye, Real dx,
                                              Real dy, Real lap, Real (&fe)[9], Real& m7eq,
                                              Real& m8eq)
@@ -199,8 +201,8 @@ __device__ __forceinline__ void f_equilibria(const NodeParams<Real>& P, Real drh
 }
 
 // Gamma mu with the chemical potential of Eq. (chempot).
-template <typename Real>
-__device__ __forceinline__ Real gamma_mu(const NodeParams<Real>& P, Real phi, Real lap)
+template <typename Real, class PP>
+__device__ __forceinline__ Real gamma_mu(PP& P, Real phi, Real lap)
 {
     const Real mu = P.a * (phi * phi * phi - phi) - P.kappa * lap;
     return P.gamma * mu;
@@ -228,8 +230,8 @@ __device__ __forceinline__ void g_equilibria(Real phi, Real G, Real uxe, Real uy
     ge[8] = div_const<12>(Ca - (puy - pux));
 }
 
-template <typename Real>
-__device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho, Real phi,
+template <typename Real, class PP>
+__device__ __forceinline__ void equilibria(PP& P, Real drho, Real phi,
                                            Real jxe, Real jye, Real uxe, Real uye, Real dx,
                                            Real dy, Real lap, Real (&fe)[9], Real (&ge)[9],
                                            Real& m7eq, Real& m8eq)
@@ -256,8 +258,8 @@ __device__ __forceinline__ void equilibria(const NodeParams<Real>& P, Real drho,
 // (the dj terms vanish and the node leaves the collision at rest).
 // The f part of Steps 1-3 at one node: returns the post-collision f and,
 // for the g update, the equilibrium velocity (zero at Step-2 nodes).
-template <typename Real, bool MRT>
-__device__ __forceinline__ void collide_f(const NodeParams<Real>& P, const Real (&f)[9], Real phi,
+template <typename Real, bool MRT, class PP>
+__device__ __forceinline__ void collide_f(PP& P, const Real (&f)[9], Real phi,
                                           Real dx, Real dy, Real lap, bool step2,
                                           bool step2_relax_j, Real (&fo)[9], Real& uxe_out,
                                           Real& uye_out)
@@ -315,8 +317,8 @@ __device__ __forceinline__ void collide_f(const NodeParams<Real>& P, const Real 
     uye_out = uye;
 }
 
-template <typename Real, bool MRT>
-__device__ __forceinline__ void collide(const NodeParams<Real>& P, const Real (&f)[9],
+template <typename Real, bool MRT, class PP>
+__device__ __forceinline__ void collide(PP& P, const Real (&f)[9],
                                         const Real (&g)[9], Real phi, Real dx, Real dy, Real lap,
                                         bool step2, bool step2_relax_j, Real (&fo)[9],
                                         Real (&go)[9])

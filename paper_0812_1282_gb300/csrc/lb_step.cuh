@@ -182,10 +182,14 @@ __device__ __forceinline__ void produce_tile(const DomDesc& D, int parity, int x
 // ----------------------------------------------------------- consumer
 // Compute warp cw (0-based among compute warps) processes its 32 columns of
 // one tile.  q: stage sequence number of the tile's first stage.
+// prm_shared, when set, holds the node parameters in shared memory; the
+// collision then reads them at each use instead of keeping them in
+// registers for the whole tile.
 template <typename Real, bool MRT, int S, int NWC = 0>
 __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x0, int y0, int rows,
                                              unsigned char* __restrict__ smem, int nw, int cw,
-                                             unsigned& q)
+                                             unsigned& q,
+                                             const NodeParams<Real>* prm_shared = nullptr)
 {
     const int NW = NWC > 0 ? NWC : nw;  // compile-time strip width when specialised
     Real* __restrict__ fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
@@ -302,7 +306,12 @@ __device__ __forceinline__ void consume_tile(const DomDesc& D, int parity, int x
                            sp[own - 1], sm[own + 1], sm[own - 1], dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
             Real fo[9], go[9];
-            collide<Real, MRT>(prm, f, g, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, go);
+            if (prm_shared) {
+                const volatile NodeParams<Real>& PV = *prm_shared;
+                collide<Real, MRT>(PV, f, g, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, go);
+            } else {
+                collide<Real, MRT>(prm, f, g, c, dx, dy, lap, s2, D.step2_relax_j != 0, fo, go);
+            }
             const int o = y * pitch + x + kXOff;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {

@@ -19,6 +19,8 @@ namespace lbfe {
 // Stage-ring depth: rows of bulk copies in flight per CTA.
 template <typename Real>
 constexpr int kStages = sizeof(Real) == 4 ? 4 : 3;
+// Named barrier of the compute warps of the batched full-storage form.
+constexpr int kComputeBarrierFull = 1;
 
 // Launch shape: blockDim.x = W + 32 (one producer warp, W / 32 compute
 // warps), W the strip width.
@@ -54,6 +56,7 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int tags[kStages<Real>];
+    __shared__ NodeParams<Real> tile_prm;  // the current tile's node parameters
     constexpr int S = kStages<Real>;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages<Real, S, NWC>(smem, NW);
@@ -84,10 +87,18 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
     } else {
         for (;;) {
             const int it = next_tag<Real, S, NWC>(smem, NW, q, tags, err);
-            if (it < 0 || it >= n_items) break;  // end of the list (or a failed wait)
+            // one decision for all compute warps (the end of the list, or a
+            // failed wait on any of them), so that they meet at the same
+            // barriers
+            if (named_sync_or(kComputeBarrierFull, 32 * NW, it < 0 || it >= n_items)) break;
             const WorkItem w = items[it];
             const DomDesc D = descs[w.dom];
-            consume_tile<Real, MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q);
+            // every compute warp is past the previous tile: refresh the shared
+            // copy of the node parameters, which the collision reads at each use
+            if (warp == 1 && lane == 0) tile_prm = node_params<Real>(D);
+            named_sync(kComputeBarrierFull, 32 * NW);
+            consume_tile<Real, MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, smem, NW, warp - 1, q,
+                                            &tile_prm);
         }
     }
 }
