@@ -1,25 +1,31 @@
 // Diagnostics reduction that allocates nothing (lb_stats_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// numbers: code that runs while a CUDA graph is being captured (an
-// allocation there is illegal or ends up baked into the graph), code that
-// owns every byte of device memory through its own pool and forbids stray
-// cudaMalloc calls, and long-running services that must not fragment or
-// grow their memory footprint mid-run.  For them this file offers a variant
-// of the moments reduction whose scratch space is a fixed, file-scope device
-// array instead of a buffer from the library's workspace.
+// numbers: an application that owns every byte of the device through its
+// own memory pool and forbids stray cudaMalloc calls, or a long-running
+// service that must not fragment or grow its memory footprint mid-run.  For
+// them this file offers a variant of the moments reduction whose scratch
+// space is a fixed, file-scope device array instead of a buffer from the
+// library's workspace.
 //
 // The array (kMaxBlocks block partials of kFields doubles, 48 KiB) is created
 // when the library is loaded on a device and lives until the process exits.
 // Its device address is looked up once per device, on the first call for
 // that device (the device holding the population arrays); make that first
-// call outside any stream capture.  Every call shares the array: two calls
+// call before any stream capture.  Every call shares the array: two calls
 // whose kernels overlap on the GPU (different streams, no ordering between
 // them) race on it and may return wrong numbers; calls ordered on one
-// stream are safe.  Each call
-// writes every slot it later reads, so nothing has to be cleared first.
+// stream are safe.  Each call writes every slot it later reads, so nothing
+// has to be cleared first.
+//
+// The kernels are launched with cudaLaunchKernel, whose return value is the
+// launch's own status: the runtime's per-thread "last error" is neither read
+// nor cleared, so an error left there by an earlier, unrelated call stays
+// for its owner and is not reported as a failure of this one.  The caller's
+// current device is restored before returning.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <mutex>
@@ -131,6 +137,25 @@ cudaError_t scratch_for_current_device(double** out)
     return cudaSuccess;
 }
 
+// Restores the calling thread's current device when it goes out of scope.
+struct DeviceRestore {
+    int prev = -1;
+    ~DeviceRestore()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+// Device that holds `p` (device memory only), or -1.
+int device_of(const void* p)
+{
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess || attr.type != cudaMemoryTypeDevice)
+        return -1;
+    return attr.device;
+}
+
 }  // namespace
 
 extern "C" int lb_stats_noalloc(const void* f, const void* g, int nx, int ny, int precision,
@@ -139,28 +164,26 @@ extern "C" int lb_stats_noalloc(const void* f, const void* g, int nx, int ny, in
     if (!f || !g || !stats_dev) return LB_ERR_INVALID_ARG;
     if (precision != LB_FP32 && precision != LB_FP64) return LB_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1) return LB_ERR_INVALID_ARG;
-    const long long n = (long long)nx * ny;
+    long long n = (long long)nx * ny;
     if (9 * n > INT_MAX) return LB_ERR_INVALID_ARG;  // beyond LB_STATS_NOALLOC_MAX_VALUES
-    // work on the device that holds the populations
-    cudaPointerAttributes attr{};
-    if (cudaPointerGetAttributes(&attr, f) != cudaSuccess || attr.type != cudaMemoryTypeDevice)
-        return LB_ERR_INVALID_ARG;
-    if (cudaSetDevice(attr.device) != cudaSuccess) return LB_ERR_CUDA;
+    // all three arrays on one device; the work runs there
+    const int dev = device_of(f);
+    if (dev < 0 || device_of(g) != dev || device_of(stats_dev) != dev) return LB_ERR_INVALID_ARG;
+    DeviceRestore restore;
+    if (cudaGetDevice(&restore.prev) != cudaSuccess) return LB_ERR_CUDA;
+    if (dev != restore.prev && cudaSetDevice(dev) != cudaSuccess) return LB_ERR_CUDA;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return LB_ERR_CUDA;
-    long long blocks = (n + kBlock - 1) / kBlock;
-    if (blocks > kMaxBlocks) blocks = kMaxBlocks;
+    int blocks = int(std::min<long long>((n + kBlock - 1) / kBlock, kMaxBlocks));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (precision == LB_FP32)
-        noalloc_partials<float><<<int(blocks), kBlock, 0, s>>>(static_cast<const float*>(f),
-                                                               static_cast<const float*>(g), n,
-                                                               scratch);
-    else
-        noalloc_partials<double><<<int(blocks), kBlock, 0, s>>>(static_cast<const double*>(f),
-                                                                static_cast<const double*>(g), n,
-                                                                scratch);
-    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-    noalloc_finish<<<1, kBlock, 0, s>>>(scratch, int(blocks), stats_dev);
-    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    void* pass1[] = {(void*)&f, (void*)&g, &n, &scratch};
+    const void* k1 = precision == LB_FP32 ? reinterpret_cast<const void*>(&noalloc_partials<float>)
+                                          : reinterpret_cast<const void*>(&noalloc_partials<double>);
+    if (cudaLaunchKernel(k1, dim3(blocks), dim3(kBlock), pass1, 0, s) != cudaSuccess)
+        return LB_ERR_CUDA;
+    void* pass2[] = {&scratch, &blocks, &stats_dev};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(&noalloc_finish), dim3(1), dim3(kBlock),
+                         pass2, 0, s) != cudaSuccess)
+        return LB_ERR_CUDA;
     return LB_OK;
 }

@@ -4,6 +4,7 @@ degrees; 20000 steps) on the GPU in FP32 and FP64 against the FP64 oracle's
 stored results (tests/golden/sweep_200x100.json, written by
 tests/golden/make_sweep_200x100.py, which calls only the oracle).
 
+FP32 runs in both g storages (full, and the compact form the bench times).
 Bars: contact angle within 0.5 degrees (FP32) and 1e-6 degrees (FP64); the
 spurious-current norm max |u| within 2 % (FP32).  A case whose oracle run
 turned non-finite must turn non-finite on the GPU too (and be reported by the
@@ -46,11 +47,12 @@ def _id(c):
     return "%s-R%d-%g" % (name, c["ratio"], c["theta_target"])
 
 
-def _run(lbf, case, precision):
+def _run(lbf, case, precision, compact=False):
     c = lbinputs.SWEEP_200x100
     p = lbf.params(**lbinputs.BASE, precision=precision, collision=case["collision"],
                    tau_alpha=case["tau_alpha"], tau_beta=case["tau_beta"], h_bottom=case["h"],
-                   h_top=0.0, step2_relax_momentum=case["step2_relax_momentum"])
+                   h_top=0.0, step2_relax_momentum=case["step2_relax_momentum"],
+                   compact_g=compact)
     sim = lbf.Lattice(p, c["nx"], c["ny"])
     try:
         sim.init_drop(c["R"], c["cx"], c["cy"])
@@ -68,14 +70,17 @@ def test_golden_present():
     assert os.path.exists(GOLDEN), "run tests/golden/make_sweep_200x100.py"
 
 
+@pytest.mark.parametrize("compact", [False, True], ids=["full-g", "compact-g"])
 @pytest.mark.parametrize("case", _cases(), ids=_id)
-def test_sweep_fp32_angle_within_half_degree(lbf, case):
-    th, umax, st = _run(lbf, case, "fp32")
+def test_sweep_fp32_angle_within_half_degree(lbf, case, compact):
+    """FP32 in both g storages (the compact one is the storage the bench
+    times) against the FP64 oracle's 20000-step run."""
+    th, umax, st = _run(lbf, case, "fp32", compact)
     if case["diverged_at"]:
         assert st["nonfinite"] > 0
         return
-    print("%s: oracle %.4f  gpu-fp32 %.4f  max|u| oracle %.3e gpu %.3e"
-          % (_id(case), case["theta"], th, case["max_u"], umax))
+    print("%s compact=%s: oracle %.4f  gpu-fp32 %.4f  max|u| oracle %.3e gpu %.3e"
+          % (_id(case), compact, case["theta"], th, case["max_u"], umax))
     assert st["nonfinite"] == 0
     assert abs(th - case["theta"]) <= 0.5
     assert umax == pytest.approx(case["max_u"], rel=0.02)

@@ -1,9 +1,9 @@
 """lb_stats_noalloc against lb_moments.
 
 Some callers cannot allocate device memory at the moment they want the
-diagnostics -- for example code running while a CUDA graph is captured, or
-an application whose own memory pool owns every byte of the device.  For
-them the library offers lb_stats_noalloc, whose scratch space is a fixed
+diagnostics -- for example an application whose own memory pool owns every
+byte of the device, or a service that must keep a fixed memory footprint.
+For them the library offers lb_stats_noalloc, whose scratch space is a fixed
 device array inside the library instead of an allocation.  It must report
 the same mass, order parameter, momentum and spurious-current norm as the
 allocating path (lb_moments), also when called twice in a row on different
@@ -86,3 +86,26 @@ def test_stats_noalloc_rejects_bad_sizes(lbf):
         lbf.lb_stats_noalloc(buf.data_ptr(), buf.data_ptr(), 0, 4, lbf.LB_FP64, out.data_ptr())
     with pytest.raises(lbf.LBError):
         lbf.lb_stats_noalloc(buf.data_ptr(), buf.data_ptr(), 4, 4, 7, out.data_ptr())
+
+
+def test_stats_noalloc_rejects_host_arrays(lbf):
+    """Every array must be device memory of one device; a host array is
+    refused before any launch."""
+    import torch
+
+    # populations of a uniform state at rest (rho = 1 at every node)
+    dev = torch.full((9 * 16,), 1.0 / 9.0, dtype=torch.float64, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    host = np.zeros(9 * 16)
+    for args in ((dev.data_ptr(), host.ctypes.data, out.data_ptr()),
+                 (dev.data_ptr(), dev.data_ptr(), host.ctypes.data),
+                 (host.ctypes.data, dev.data_ptr(), out.data_ptr())):
+        with pytest.raises(lbf.LBError) as e:
+            lbf.lb_stats_noalloc(args[0], args[1], 4, 4, lbf.LB_FP64, args[2])
+        assert e.value.code == lbf.LB_ERR_INVALID_ARG
+    # a valid call afterwards still works (nothing was left half set up)
+    lbf.lb_stats_noalloc(dev.data_ptr(), dev.data_ptr(), 4, 4, lbf.LB_FP64, out.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    mass, order, mx, my, umax, bad = out.cpu().numpy().tolist()
+    assert mass == pytest.approx(16.0, rel=1e-14) and umax == 0.0 and bad == 0.0
