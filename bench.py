@@ -17,8 +17,9 @@ FP64 build (ALU-bound on GB300) and the batched 256-domain workload against
 a per-domain launch loop.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs its own replica (weak scaling, no collective
-on the data path); rank 0 prints.
+Under torchrun each rank runs its own replica of the headline lattice (weak
+scaling, no collective on the data path) and a node-balanced share of the
+batched workload's domains; rank 0 prints.
 """
 from __future__ import annotations
 
@@ -42,14 +43,20 @@ sys.path.insert(0, ROOT)
 import lbinputs  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-FP64_OPS_PER_CLK_SM = 2  # GB300: 2 FP64 operations (DFMA, DADD, DMUL) per clock per SM
 BYTES_PER_NODE = {"fp32": 144, "fp64": 288, "fp32c": 104}  # fp32c: compact g storage
+
+
+# Device-code sources of the step kernels: an ncu figure recorded under
+# profiles/ stays valid while these are unchanged.
+KERNEL_SOURCES = ("lb_async.cuh", "lb_internal.h", "lb_node.cuh", "lb_node_x2.cuh", "lb_step.cuh",
+                  "lb_step_compact.cuh", "lb_step_kernels.cuh", "lb_step_f32.cu",
+                  "lb_step_f64.cu")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0812_1282_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_0812_1282_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -278,11 +285,21 @@ def run_e2e(lbf, torch, steps, compact=False, tile=None):
                               "phi_readback": split[2]})
 
 
+def fp64_pipe_peak(lbf):
+    """Measured FP64 operations per second of this GPU, per operation kind
+    (lb_fp64_peak: independent DFMA, DADD or DMUL chains over the whole
+    GPU), best of three runs each."""
+    out = {}
+    for kind, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+        out[name] = max(lbf.lb_fp64_peak(kind) for _ in range(3))
+    return out
+
+
 def run_fp64(lbf, torch, steps, size=None, tile=None):
     """The headline workload in FP64 storage and arithmetic.  On this GPU
     the step is bound by the FP64 pipe, so besides its bytes it reports the
-    pipe's operations per second against its peak (2 per clock per SM), with
-    the operations per node counted by ncu
+    pipe's operations per second against the pipe's measured peak
+    (lb_fp64_peak), with the operations per node counted by ncu
     (profiles/lb_step_mrt_fp64_2048.txt)."""
     c = lbinputs.SPINODAL_8192
     side = size or c["nx"]
@@ -295,27 +312,41 @@ def run_fp64(lbf, torch, steps, size=None, tile=None):
     else:
         tile = sim.autotune(reps=1)
     sim.step(2)
-    dt = time_steps(sim, steps, torch)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        dt = time_steps(sim, steps, torch)
     sim.close()
+    with ClockSampler(torch.cuda.current_device()) as clk_peak:
+        peak = fp64_pipe_peak(lbf)
     res = dict(mlups=n * steps / dt / 1e6, seconds_per_step=dt / steps, tile=list(tile[:2]),
-               gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9, bound="alu")
+               gbs=n * BYTES_PER_NODE["fp64"] * steps / dt / 1e9, bound="alu",
+               clocks=clk.summary())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk_peak.summary().get("sm_mhz") or sm_max_mhz()
+    res["pipe_peak_measured"] = {
+        k + "_gops": round(v / 1e9, 1) for k, v in peak.items()}
+    res["pipe_peak_measured"].update(
+        {k + "_per_clk_per_sm": round(v / (sms * mhz * 1e6), 3) for k, v in peak.items()},
+        sm_mhz=mhz, source="lb_fp64_peak: independent dependency chains of one FP64 operation "
+                           "over the whole GPU, CUDA events, best of 3")
     # the FP64 pipe takes one DADD, DMUL or DFMA per slot: its roofline counts
-    # those operations (a DFMA is two flops, the others one)
-    opn = profile_value("lb_step_mrt_fp64_2048", "fp64_ops_per_node")
-    fpn = profile_value("lb_step_mrt_fp64_2048", "fp64_flops_per_node")
+    # those operations (a DFMA is two flops, the others one); the peak of the
+    # step's own mix of the three kinds is the harmonic mean weighted by the
+    # per-node counts ncu measured
+    prof = "lb_step_mrt_fp64_2048"
+    cnt = {k: profile_value(prof, k + "_per_node") for k in ("dfma", "dadd", "dmul")}
+    opn = profile_value(prof, "fp64_ops_per_node")
+    fpn = profile_value(prof, "fp64_flops_per_node")
     res["fp64_ops_per_node"] = opn
     res["fp64_flops_per_node"] = fpn
-    if opn is not None and fpn is not None:
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
-        ghz = sm_max_mhz() / 1e3
+    if opn is not None and all(v is not None for v in cnt.values()):
+        mix_peak = opn / sum(cnt[k] / peak[k] for k in cnt)   # operations per second
         rate = n * steps / dt
         res.update(achieved_gops=round(rate * opn / 1e9, 1),
-                   peak_gops=round(FP64_OPS_PER_CLK_SM * sms * ghz, 1),
-                   frac=round(rate * opn / 1e9 / (FP64_OPS_PER_CLK_SM * sms * ghz), 4),
+                   peak_gops=round(mix_peak / 1e9, 1),
+                   frac=round(rate * opn / mix_peak, 4),
                    achieved_tflops=round(rate * fpn / 1e12, 4),
-                   peak_tflops=round(2 * FP64_OPS_PER_CLK_SM * sms * ghz / 1e3, 4),
-                   peak_source="derived: 2 FP64 pipe operations per clock per SM x SMs x "
-                               "max SM clock")
+                   peak_source="measured: lb_fp64_peak per kind, weighted by the step's "
+                               "operation mix (ncu counts per node)")
     return res
 
 
@@ -372,40 +403,104 @@ def run_capillary(lbf, torch, steps=None):
                      "half, theory gamma w cos(theta_a) / 6")
 
 
-def run_batched(lbf, torch, steps, compact=False):
-    """256 sessile drops (sides 64..512) in one launch per step, against the
-    same domains stepped one after another (one launch per domain per step)."""
+BATCH_JOB_STEPS = 10000
+BATCH_GOLDEN = os.path.join(ROOT, "tests", "golden", "batch_angles.json")
+
+
+def batch_params(lbf, specs, compact):
+    # the momentum-relaxing reading of Step 2: with the literal rates 19 of
+    # the 256 drops (high angle, viscosity ratio 10) go non-finite within the
+    # 10000-step job; the throughput is the same either way
+    return [lbf.params(collision="mrt", precision="fp32", tau_alpha=s["tau_alpha"],
+                       tau_beta=s["tau_beta"], h_bottom=lbf.lb_wetting_h(s["theta"]),
+                       step2_relax_momentum=True, compact_g=compact) for s in specs]
+
+
+def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_steps=None):
+    """The 256 sessile drops (sides 64..512) of the batched workload: the
+    whole 10000-step job in one batched handle per GPU (the autotuner picks
+    the schedule), timed from the first step to the last; then, on a single
+    GPU, the same domains stepped one launch per domain per step (each
+    domain with its own tuned launch shape), timed over `loop_steps` steps
+    and scaled to the job.  Under torchrun every rank takes a node-balanced
+    share of the domains (no data-path collective) and the per-domain
+    results are gathered at the end."""
+    from paper_0812_1282_gb300 import shard
+
+    job = job_steps or BATCH_JOB_STEPS
     specs = lbinputs.batch_specs()
-    plist, nxs, nys = [], [], []
-    for s in specs:
-        # the momentum-relaxing reading of Step 2: with the literal rates 19 of
-        # the 256 drops (high angle, viscosity ratio 10) go non-finite within
-        # the 10000-step job; the throughput is the same either way
-        plist.append(lbf.params(collision="mrt", precision="fp32", tau_alpha=s["tau_alpha"],
-                                tau_beta=s["tau_beta"], h_bottom=lbf.lb_wetting_h(s["theta"]),
-                                step2_relax_momentum=True, compact_g=compact))
-        nxs.append(s["nx"])
-        nys.append(s["ny"])
-    nodes = sum(a * b for a, b in zip(nxs, nys))
-    batch = lbf.Batch(plist, nxs, nys)
-    for d, s in enumerate(specs):
-        batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    plist = batch_params(lbf, specs, compact)
+    nodes_d = [s["nx"] * s["ny"] for s in specs]
+    parts = shard.partition(nodes_d, ws)
+    mine = parts[rank]
+    bp = [plist[d] for d in mine]
+    batch = lbf.Batch(bp, [specs[d]["nx"] for d in mine], [specs[d]["ny"] for d in mine])
+
+    def init():
+        for k, d in enumerate(mine):
+            batch.init_drop(specs[d]["R"], specs[d]["cx"], specs[d]["cy"], dom=k)
+
+    init()
     tile = batch.autotune(reps=2)
-    batch.step(4)
-    dt_b = time_steps(batch, steps, torch)
+    sched = batch.schedule()
+    batch.step(128)  # builds the step graphs
+    init()
+    torch.cuda.synchronize()
+    launches0 = batch.launch_count
+    barrier(ws)
+    dt_b = max_over_ranks(ws, time_steps(batch, job, torch))
+    launches = batch.launch_count - launches0
+    # per-domain results of the timed job: angle, max |u|, non-finite count
+    rows = {}
+    for k, d in enumerate(mine):
+        st = batch.stats(dom=k)
+        try:
+            th = batch.contact_angle(dom=k)[0] if st["nonfinite"] == 0 else float("nan")
+        except lbf.LBError:
+            th = float("nan")
+        rows[d] = [th, st["max_u"], float(st["nonfinite"])]
     batch.close()
+    table = shard.gather_rows(len(specs), 3, rows, device="cuda" if ws > 1 else "cpu")
+    nodes = sum(nodes_d)
+    bpn = BYTES_PER_NODE["fp32c" if compact else "fp32"]
+    res = dict(domains=len(specs), nodes=nodes, steps_timed=job, job_seconds=round(dt_b, 4),
+               batched_mlups=nodes * job / dt_b / 1e6,
+               batched_sims_per_s=len(specs) / dt_b,
+               achieved_gbs=round(nodes * job * bpn / dt_b / 1e9, 1),
+               algorithmic_bytes_per_node=bpn,
+               gpu_launches=launches,
+               schedule=sched, tile=list(tile[:2]),
+               storage="compact g" if compact else "full",
+               nonfinite_domains=sum(1 for r in table if r[2] > 0))
+    if ws > 1:
+        res.update(parallelism="%d ranks, node-balanced split of the domains (greedy, "
+                               "largest first), no data-path collective" % ws,
+                   nodes_per_rank=shard.rank_loads(nodes_d, parts))
+    # angle error of the timed run against the FP64 oracle's stored angles
+    if os.path.exists(BATCH_GOLDEN):
+        with open(BATCH_GOLDEN) as fh:
+            gold = json.load(fh)
+        if gold["steps"] == job:
+            errs = [abs(table[r["dom"]][0] - r["relax"]["theta"]) for r in gold["domains"]
+                    if not r["relax"]["diverged"]]
+            res["angle_err_max_deg"] = max(errs) if errs else None
+            res["angle_err_domains"] = len(errs)
+    if ws > 1 or rank != 0:
+        return res
+    # the per-domain launch loop, each domain with its own tuned launch shape
     sims = []
     for d, s in enumerate(specs):
-        sim = lbf.Lattice(plist[d], nxs[d], nys[d])
+        sim = lbf.Lattice(plist[d], s["nx"], s["ny"])
         sim.init_drop(s["R"], s["cx"], s["cy"])
-        sim.set_tile(*tile[:2])
+        sim.autotune(reps=2)
+        sim.init_drop(s["R"], s["cx"], s["cy"])
         sim.step(2)
         sims.append(sim)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(steps):
+    for _ in range(loop_steps):
         for sim in sims:
             sim.step(1)
     e1.record()
@@ -413,28 +508,33 @@ def run_batched(lbf, torch, steps, compact=False):
     dt_l = e0.elapsed_time(e1) / 1e3
     # stronger loop: each domain runs all its steps back to back from its own
     # captured CUDA graphs, one domain after another
+    for sim in sims:
+        sim.step(64)  # builds each domain's graphs
+    torch.cuda.synchronize()
     e0.record()
     for sim in sims:
-        sim.step(steps)
+        sim.step(loop_steps)
     e1.record()
     torch.cuda.synchronize()
     dt_g = e0.elapsed_time(e1) / 1e3
     for sim in sims:
         sim.close()
-    full = 10000
-    return dict(domains=len(specs), nodes=nodes, steps_timed=steps,
-                batched_mlups=nodes * steps / dt_b / 1e6, loop_mlups=nodes * steps / dt_l / 1e6,
-                loop_graph_mlups=nodes * steps / dt_g / 1e6,
-                batched_sims_per_s=len(specs) / (dt_b / steps * full),
-                loop_sims_per_s=len(specs) / (dt_l / steps * full),
-                loop_graph_sims_per_s=len(specs) / (dt_g / steps * full),
-                speedup_vs_loop=dt_l / dt_b, speedup_vs_loop_graph=dt_g / dt_b,
-                tile=list(tile[:2]), storage="compact g" if compact else "full",
-                note="sims/s of the 10000-step job, from %d timed steps; loop = one launch "
-                     "per domain per step; loop_graph = each domain's steps replayed from "
-                     "its own CUDA graphs, domains in sequence; MRT with the momentum-"
-                     "relaxing Step-2 reading (all 256 drops stay finite; angles within "
-                     "0.5 deg of the FP64 oracle, tests/test_gpu_batch_angles.py)" % steps)
+    scale = job / loop_steps
+    res.update(loop_mlups=nodes * loop_steps / dt_l / 1e6,
+               loop_graph_mlups=nodes * loop_steps / dt_g / 1e6,
+               loop_sims_per_s=len(specs) / (dt_l * scale),
+               loop_graph_sims_per_s=len(specs) / (dt_g * scale),
+               speedup_vs_loop=dt_l * scale / dt_b, speedup_vs_loop_graph=dt_g * scale / dt_b,
+               note="batched: the whole %d-step job timed (CUDA events, one batched handle, "
+                    "schedule from lb_autotune); loop = one launch per domain per step, each "
+                    "domain with its own autotuned launch shape; loop_graph = each domain's "
+                    "steps replayed from its own CUDA graphs, domains in sequence; both loops "
+                    "timed over %d steps and scaled to the job; MRT with the momentum-"
+                    "relaxing Step-2 reading; angle_err_max_deg = the timed run's angles "
+                    "against the FP64 oracle's (tests/golden/batch_angles.json, 16 smallest "
+                    "domains, compact and full storage both tested in "
+                    "tests/test_gpu_batch_angles.py)" % (job, loop_steps))
+    return res
 
 
 def cpu_baseline(seconds=12.0):
@@ -505,7 +605,10 @@ def ours(args):
     if args.only:
         # one extra workload alone (profiling aid): its JSON object only
         if args.only == "batched":
-            res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact")
+            res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact",
+                              ws=ws, rank=rank, job_steps=args.job_steps)
+            if rank != 0:
+                return
         elif args.only == "fp64":
             tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
             res = run_fp64(lbf, torch, max(3, args.steps), size=args.size, tile=tile)
@@ -594,6 +697,12 @@ def ours(args):
             extras["capillary"] = {"error": str(exc)}
         line["extras"] = extras
         line["cpu_baseline"] = cpu_baseline()
+    elif ws > 1 and not args.quick:
+        # the batched workload split over the ranks (node-balanced domains)
+        res = run_batched(lbf, torch, compact=compact, ws=ws, rank=rank,
+                          job_steps=args.job_steps)
+        if rank == 0:
+            line["extras"] = {"batched": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -743,6 +852,8 @@ def main():
                     help="g storage of the headline lattice (compact: phi, Gamma mu, u_eq)")
     ap.add_argument("--only", choices=("batched", "capillary", "fp64"), default=None,
                     help="run one extra workload alone for --steps steps (profiling aid)")
+    ap.add_argument("--job-steps", type=int, default=None,
+                    help="steps of the batched job (profiling aid; default 10000)")
     ap.add_argument("--experiment", choices=("ramp", "stripe"), default=None,
                     help="run a physics experiment instead of the benchmark and print its "
                          "JSON table (ramp: the quasi-static wetting ramp of Sec. IV; stripe: "

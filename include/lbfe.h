@@ -268,13 +268,58 @@ int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes);
 
 /* Launch shape: threads per CTA along x (block_x, a multiple of 32 in
  * [32, 256]) and rows each CTA marches through (rows >= 1).  Results do not
- * depend on it.  Invalidates captured graphs. */
+ * depend on it.  On a batch it sets a one-class schedule with that shape
+ * (lb_schedule).  Invalidates captured graphs. */
 int lb_set_tile(lb_handle* h, int block_x, int rows);
 int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
 
-/* Autotuner: times each candidate launch shape for `reps` steps on the
- * device (without advancing the state) and keeps the fastest.  Outputs may
- * be NULL. */
+/* Schedule of a batch (lb_create_batch; the configurations' many independent
+ * domains, which the paper does not treat): how the (domain, strip, row
+ * block) work of one time step is cut and spread over the GPU.
+ *  n_class:     1..LB_MAX_SCHED_CLASSES domain-size classes.  Class k takes
+ *               the domains with max_nx[k-1] < nx <= max_nx[k] (max_nx[-1] =
+ *               0); the last class takes every wider domain (its max_nx is
+ *               ignored).  Each class has its own launch per step.
+ *  block_x[k], rows[k]: the launch shape of class k, as lb_set_tile (a
+ *               strip of block_x columns, or with compact g storage two
+ *               columns per compute thread less a 4-column halo, and `rows`
+ *               rows per work item).
+ *  ctas_per_sm[k]: 0 gives one CTA per work item (the hardware spreads
+ *               them); n >= 1 a persistent grid of n CTAs per SM that take
+ *               work items from a device counter.
+ *  order:       0 work items by domain, then row block, then strip; 1
+ *               largest item first (the small ragged items come last, which
+ *               shortens the tail of each launch).
+ *  chains:      with several classes, 1 lets each class advance through the
+ *               steps of a captured graph as its own chain of launches
+ *               (the classes hold disjoint domains, so they only meet at the
+ *               graph's end); 0 launches the classes one after the other
+ *               every step.
+ * Results do not depend on the schedule (bit for bit).  A single-domain
+ * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
+ * Errors: LB_ERR_INVALID_ARG for a value out of range or max_nx not
+ * increasing. */
+#define LB_MAX_SCHED_CLASSES 4
+typedef struct lb_schedule {
+    int n_class;
+    int max_nx[LB_MAX_SCHED_CLASSES];
+    int block_x[LB_MAX_SCHED_CLASSES];
+    int rows[LB_MAX_SCHED_CLASSES];
+    int ctas_per_sm[LB_MAX_SCHED_CLASSES];
+    int order;
+    int chains;
+} lb_schedule;
+int lb_set_schedule(lb_handle* h, const lb_schedule* s);
+int lb_get_schedule(const lb_handle* h, lb_schedule* s);
+
+/* Autotuner: times each candidate for `reps` repetitions on the device
+ * (without advancing the state) and keeps the fastest.  A single domain
+ * tries launch shapes (block_x x rows).  A batch tries schedules
+ * (lb_schedule): one class or two size classes with their own strip widths,
+ * rows per work item, persistent or one-CTA-per-item grids, and the item
+ * order, each timed as a captured graph of several steps.  Outputs (class
+ * 0's shape and the best time per step in ms) may be NULL; lb_get_schedule
+ * returns the whole choice. */
 int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms);
 
 /* Steps taken since the last initialisation (host-side count). */
@@ -300,29 +345,43 @@ const char* lb_last_error(void);
  * launch error.  Synchronises `stream`; leaves the context usable. */
 int lb_check_wait_timeout(void* stream);
 
+/* Measured FP64 throughput of the current device (the paper has no
+ * counterpart: the roofline denominator of the FP64 build, which the FP64
+ * pipe bounds).  A grid that fills the GPU runs independent dependency
+ * chains of one operation -- kind 0 DFMA, 1 DADD, 2 DMUL -- and the
+ * operations per second (a DFMA counts as one operation, two flops) over the
+ * event-timed duration go to *ops_per_s.  Runs on `stream` (NULL = legacy
+ * default) and synchronises it; allocates and frees a small buffer.
+ * Errors: LB_ERR_INVALID_ARG for an unknown kind or a NULL output,
+ * LB_ERR_CUDA on a CUDA failure. */
+int lb_fp64_peak(int kind, void* stream, double* ops_per_s);
+
 /* Diagnostics without any allocation (the paper has no counterpart: this is
  * a service for callers that may not allocate device memory at the time
- * they need the numbers -- code running inside a CUDA graph capture, code
- * that owns all device memory through its own pool, long-running services
- * that must keep a fixed footprint).
+ * they need the numbers -- an application that owns all device memory
+ * through its own pool and forbids other allocations, or a long-running
+ * service that must keep a fixed memory footprint).
  *  f, g:      device arrays [9][ny][nx] of absolute populations (the layout
  *             lb_get_populations returns), float for LB_FP32, double for
- *             LB_FP64; owned by the caller.  The call runs on the device
- *             that holds f.
+ *             LB_FP64; owned by the caller.
  *  stats_dev: device array of 6 doubles, owned by the caller, receiving
  *             sum rho, sum phi, sum rho u_x, sum rho u_y, max |u| and the
  *             number of nodes whose moments are not finite.
- * Work is enqueued on `stream` (cudaStream_t, NULL = legacy default) and
- * nothing is synchronised.  The scratch space is a fixed device array of
- * 1024 block partials (48 KiB) that the library carries on every device it
- * is loaded on until the process exits; its address is looked up on the
- * first call made on a device, so make that first call outside any stream
- * capture.  All calls share that array: calls that may overlap on the GPU
- * (unordered streams) race and can return wrong numbers.  At most
- * LB_STATS_NOALLOC_MAX_VALUES population values per array (9 * nx * ny);
- * larger inputs, nx or ny < 1, NULL pointers or an unknown precision give
- * LB_ERR_INVALID_ARG; a failed launch gives LB_ERR_CUDA.  No cudaMalloc,
- * cudaFree or other allocating call is made. */
+ * f, g and stats_dev must be device memory of one device; the work runs on
+ * that device and is enqueued on `stream` (cudaStream_t of that device, NULL
+ * = its legacy default stream); nothing is synchronised.  The calling
+ * thread's current device is left as it was.  The scratch space is a fixed
+ * device array of 1024 block partials (48 KiB) that the library carries on
+ * every device it is loaded on until the process exits; its address is
+ * looked up on the first call made on a device, so make that first call
+ * before any stream capture.  All calls share that array: calls that may
+ * overlap on the GPU (unordered streams) race and can return wrong numbers.
+ * At most LB_STATS_NOALLOC_MAX_VALUES population values per array
+ * (9 * nx * ny); larger inputs, nx or ny < 1, NULL or non-device pointers,
+ * arrays on different devices or an unknown precision give
+ * LB_ERR_INVALID_ARG; a failed launch gives LB_ERR_CUDA (the launch status
+ * itself: the runtime's last-error state is neither read nor cleared).  No
+ * cudaMalloc, cudaFree or other allocating call is made. */
 #define LB_STATS_NOALLOC_MAX_VALUES 2147483647LL
 int lb_stats_noalloc(const void* f, const void* g, int nx, int ny, int precision,
                      double* stats_dev, void* stream);

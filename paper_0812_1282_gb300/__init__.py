@@ -38,8 +38,10 @@ EXPORTS = (
     "lb_save_state", "lb_load_state", "lb_set_tile", "lb_get_tile", "lb_autotune",
     "lb_step_count", "lb_sync", "lb_launch_count", "lb_error_string", "lb_last_error",
     "lb_stats_noalloc", "lb_check_wait_timeout", "lb_set_geometry", "lb_get_geometry",
-    "lb_init_channel", "lb_meniscus", "lb_set_wetting",
+    "lb_init_channel", "lb_meniscus", "lb_set_wetting", "lb_set_schedule", "lb_get_schedule",
+    "lb_fp64_peak",
 )
+LB_MAX_SCHED_CLASSES = 4
 
 
 class LBError(RuntimeError):
@@ -71,6 +73,42 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Schedule(ctypes.Structure):
+    """lb_schedule: how a batch's work is cut and spread (include/lbfe.h)."""
+    _fields_ = [
+        ("n_class", ctypes.c_int),
+        ("max_nx", ctypes.c_int * LB_MAX_SCHED_CLASSES),
+        ("block_x", ctypes.c_int * LB_MAX_SCHED_CLASSES),
+        ("rows", ctypes.c_int * LB_MAX_SCHED_CLASSES),
+        ("ctas_per_sm", ctypes.c_int * LB_MAX_SCHED_CLASSES),
+        ("order", ctypes.c_int), ("chains", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        n = self.n_class
+        return {"n_class": n, "max_nx": list(self.max_nx)[:max(n - 1, 0)],
+                "block_x": list(self.block_x)[:n], "rows": list(self.rows)[:n],
+                "ctas_per_sm": list(self.ctas_per_sm)[:n], "order": self.order,
+                "chains": self.chains}
+
+
+def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1) -> Schedule:
+    """Schedule block; block_x, rows and ctas_per_sm are per class (an int
+    applies to every class); max_nx gives the class limits (n_class - 1
+    values)."""
+    n = len(max_nx) + 1
+
+    def per_class(v):
+        v = list(v) if isinstance(v, (list, tuple)) else [v] * n
+        assert len(v) == n
+        return v + [v[0]] * (LB_MAX_SCHED_CLASSES - n)
+
+    arr = ctypes.c_int * LB_MAX_SCHED_CLASSES
+    return Schedule(n, arr(*(list(max_nx) + [0] * (LB_MAX_SCHED_CLASSES - len(max_nx)))),
+                    arr(*per_class(block_x)), arr(*per_class(rows)), arr(*per_class(ctas_per_sm)),
+                    int(order), int(chains))
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,
@@ -142,6 +180,9 @@ def lib():
                 "lb_init_channel": (i, [_H, i, i, i, d, d]),
                 "lb_meniscus": (i, [_H, i, i, i, i, i, d, _D, _D, _D]),
                 "lb_set_wetting": (i, [_H, i, d, d]),
+                "lb_set_schedule": (i, [_H, ctypes.POINTER(Schedule)]),
+                "lb_get_schedule": (i, [_H, ctypes.POINTER(Schedule)]),
+                "lb_fp64_peak": (i, [i, vp, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -185,6 +226,14 @@ def lb_stats_noalloc(f_dev_ptr, g_dev_ptr, nx, ny, precision, stats_dev_ptr, str
     if rc != LB_OK:  # this entry point leaves no message behind (it allocates nothing)
         raise LBError(rc, "lb_stats_noalloc: %s" % L.lb_error_string(rc).decode())
     return rc
+
+
+def lb_fp64_peak(kind=0, stream_ptr=0) -> float:
+    """Measured FP64 operations per second of the current device (kind 0
+    DFMA, 1 DADD, 2 DMUL; see include/lbfe.h)."""
+    v = ctypes.c_double()
+    _check(lib().lb_fp64_peak(int(kind), ctypes.c_void_p(stream_ptr), ctypes.byref(v)))
+    return v.value
 
 
 def lb_check_wait_timeout(stream_ptr=0) -> int:
@@ -353,6 +402,14 @@ class _HandleBase:
         bx, r = ctypes.c_int(), ctypes.c_int()
         _check(lib().lb_get_tile(self.h, ctypes.byref(bx), ctypes.byref(r)))
         return bx.value, r.value
+
+    def set_schedule(self, sched: Schedule):
+        _check(lib().lb_set_schedule(self.h, ctypes.byref(sched)))
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(lib().lb_get_schedule(self.h, ctypes.byref(sc)))
+        return sc.as_dict()
 
     def autotune(self, reps=5):
         bx, r, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

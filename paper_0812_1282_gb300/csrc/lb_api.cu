@@ -124,7 +124,7 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
     L.err = off;
     off = align_up(off + sizeof(unsigned), kAlign);
     L.sched = off;
-    off = align_up(off + 2 * sizeof(int), kAlign);
+    off = align_up(off + 2 * sizeof(int) * LB_MAX_SCHED_CLASSES, kAlign);
     L.staging = off;
     off = align_up(off + sizeof(double) * 4 * L.staging_nodes, kAlign);
     L.total = off;
@@ -181,9 +181,14 @@ struct lb_handle {
     cudaStream_t cap_stream = nullptr;
     int device = 0;
     int sm_count = 0;
-    int block_x = 128, rows = 32;
-    int grid_persistent = 0;  // 0: one CTA per work item
-    int schedule = 0;         // 0 domain order, 1 largest domain first
+    // Launch shape of a single domain (class 0's) and the batch schedule;
+    // cls_begin / cls_count: each class's slice of the device work list.
+    lb_schedule sched{};
+    int cls_begin[LB_MAX_SCHED_CLASSES] = {0}, cls_count[LB_MAX_SCHED_CLASSES] = {0};
+    // streams and events of the launch chains of classes 1.. in a graph
+    cudaStream_t chain[LB_MAX_SCHED_CLASSES - 1] = {nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[LB_MAX_SCHED_CLASSES - 1] = {nullptr};
     int n_items = 0;
     int parity = 0;
     long long steps = 0;
@@ -200,7 +205,10 @@ struct lb_handle {
     int* d_count() const { return reinterpret_cast<int*>(base + L.count); }
     double* d_staging() const { return reinterpret_cast<double*>(base + L.staging); }
     unsigned* d_err() const { return reinterpret_cast<unsigned*>(base + L.err); }
-    int* d_sched() const { return reinterpret_cast<int*>(base + L.sched); }
+    // two device ints per schedule class (tile counter, finished CTAs)
+    int* d_sched(int c) const { return reinterpret_cast<int*>(base + L.sched) + 2 * c; }
+    int block_x() const { return sched.block_x[0]; }
+    int rows() const { return sched.rows[0]; }
     size_t elem() const { return precision == LB_FP32 ? 4 : 8; }
 };
 
@@ -212,41 +220,62 @@ void clear_graphs(lb_handle* h)
     h->graphs.clear();
 }
 
-// Work list for the batched kernel: every (domain, x strip, row block).
+// Class of a domain under the handle's schedule.
+int class_of(const lb_handle* h, int nx)
+{
+    for (int c = 0; c + 1 < h->sched.n_class; ++c)
+        if (nx <= h->sched.max_nx[c]) return c;
+    return h->sched.n_class - 1;
+}
+
+// Work list for the batched kernel: every (domain, x strip, row block),
+// grouped by schedule class (class c's items are one contiguous slice).
 int build_items(lb_handle* h)
 {
+    for (int c = 0; c < LB_MAX_SCHED_CLASSES; ++c) h->cls_begin[c] = h->cls_count[c] = 0;
     if (h->n_dom == 1) {
         h->n_items = 0;
         return LB_OK;
     }
-    std::vector<int> order(h->n_dom);
-    for (int d = 0; d < h->n_dom; ++d) order[d] = d;
-    if (h->schedule == 1)
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return (long long)h->descs[a].nx * h->descs[a].ny >
-                   (long long)h->descs[b].nx * h->descs[b].ny;
-        });
     std::vector<WorkItem> items;
-    for (int d : order) {
-        const DomDesc& D = h->descs[d];
-        if (D.cls) continue;  // stepped by the obstacle kernels
-        if (D.compact) {
-            // the compact step's strips leave room for four halo columns; a
-            // domain is cut into near-equal strips (multiples of 4 columns,
-            // so every bulk copy stays 16-byte aligned) instead of full
-            // strips and one narrow remainder
-            const int wmax = lbfe::compact_strip(h->block_x);
-            const int k = (D.nx + wmax - 1) / wmax;
-            const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
-            for (int y0 = 0; y0 < D.ny; y0 += h->rows)
-                for (int x0 = 0; x0 < D.nx; x0 += w)
-                    items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0),
-                                             std::min(w, D.nx - x0)});
-            continue;
+    for (int c = 0; c < h->sched.n_class; ++c) {
+        const int bx = h->sched.block_x[c], rows = h->sched.rows[c];
+        std::vector<WorkItem> mine;
+        for (int d = 0; d < h->n_dom; ++d) {
+            const DomDesc& D = h->descs[d];
+            if (D.cls || class_of(h, D.nx) != c) continue;  // obstacles: their own kernels
+            if (D.compact) {
+                // the compact step's strips leave room for four halo columns; a
+                // domain is cut into near-equal strips (multiples of 4 columns,
+                // so every bulk copy stays 16-byte aligned) instead of full
+                // strips and one narrow remainder
+                const int wmax = lbfe::compact_strip(bx);
+                const int k = (D.nx + wmax - 1) / wmax;
+                const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
+                for (int y0 = 0; y0 < D.ny; y0 += rows)
+                    for (int x0 = 0; x0 < D.nx; x0 += w)
+                        mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0),
+                                                std::min(w, D.nx - x0)});
+                continue;
+            }
+            for (int y0 = 0; y0 < D.ny; y0 += rows)
+                for (int x0 = 0; x0 < D.nx; x0 += bx)
+                    mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0), 0});
         }
-        for (int y0 = 0; y0 < D.ny; y0 += h->rows)
-            for (int x0 = 0; x0 < D.nx; x0 += h->block_x)
-                items.push_back(WorkItem{d, x0, y0, std::min(h->rows, D.ny - y0), 0});
+        if (h->sched.order == 1) {
+            // largest first: nodes of the item (the full-storage strip is
+            // bx wide, clipped to the domain)
+            auto size = [&](const WorkItem& w) {
+                const int cols = w.cols > 0 ? w.cols : std::min(bx, h->descs[w.dom].nx - w.x0);
+                return (long long)cols * w.rows;
+            };
+            std::stable_sort(mine.begin(), mine.end(), [&](const WorkItem& a, const WorkItem& b) {
+                return size(a) > size(b);
+            });
+        }
+        h->cls_begin[c] = int(items.size());
+        h->cls_count[c] = int(mine.size());
+        items.insert(items.end(), mine.begin(), mine.end());
     }
     if ((long long)items.size() > h->L.item_cap)
         return fail(LB_ERR_INVALID_ARG, "work list exceeds its capacity");
@@ -258,20 +287,38 @@ int build_items(lb_handle* h)
     return LB_OK;
 }
 
-// One time step of every domain: the staged kernel for the domains without
-// obstacles (one launch: the single-domain grid, or the persistent kernel
-// over the batch's work list), then two launches per domain with obstacles.
-int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
+// Grid of class c's launch: a persistent grid, or one CTA per work item.
+int class_grid(const lb_handle* h, int c)
 {
-    const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
-    if (plain) {
-        const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
-                                        h->n_dom > 1 ? h->d_items() : nullptr, h->n_items,
-                                        h->n_dom, parity, h->block_x, h->rows,
-                                        h->grid_persistent, h->d_sched(), s);
-        if (e != 0)
-            return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
-    }
+    const int k = h->sched.ctas_per_sm[c];
+    return k > 0 ? std::min(k * h->sm_count, std::max(h->cls_count[c], 1)) : 0;
+}
+
+// The staged-kernel launch of schedule class c (batch) for one step.
+int launch_class(lb_handle* h, int c, int parity, cudaStream_t s)
+{
+    const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
+                                    h->d_items() + h->cls_begin[c], h->cls_count[c], h->n_dom,
+                                    parity, h->sched.block_x[c], h->sched.rows[c],
+                                    class_grid(h, c), h->d_sched(c), s);
+    if (e != 0)
+        return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    return LB_OK;
+}
+
+// Kernel launches of one time step.
+long long launches_per_step(const lb_handle* h)
+{
+    long long n = 0;
+    if (h->n_dom == 1)
+        n = h->descs[0].cls == nullptr ? 1 : 0;
+    else
+        for (int c = 0; c < h->sched.n_class; ++c) n += h->cls_count[c] > 0;
+    return n + 2LL * h->n_geo;
+}
+
+int enqueue_geo(lb_handle* h, int parity, cudaStream_t s)
+{
     if (h->n_geo > 0)
         for (const DomDesc& D : h->descs) {
             if (!D.cls) continue;
@@ -283,25 +330,83 @@ int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
     return LB_OK;
 }
 
-// Kernel launches of one time step.
-long long launches_per_step(const lb_handle* h)
+// One time step of every domain: the staged kernel for the domains without
+// obstacles (one launch for a single domain; one per schedule class for a
+// batch, one after the other), then two launches per domain with obstacles.
+int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
 {
-    const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
-    return (plain ? 1 : 0) + 2LL * h->n_geo;
+    if (h->n_dom == 1) {
+        if (h->descs[0].cls == nullptr) {
+            const int e = lbfe::launch_step(h->precision, h->coll, h->descs[0], h->d_descs(),
+                                            nullptr, 0, 1, parity, h->block_x(), h->rows(), 0,
+                                            h->d_sched(0), s);
+            if (e != 0)
+                return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+        }
+    } else {
+        for (int c = 0; c < h->sched.n_class; ++c) {
+            if (h->cls_count[c] == 0) continue;
+            const int rc = launch_class(h, c, parity, s);
+            if (rc != LB_OK) return rc;
+        }
+    }
+    return enqueue_geo(h, parity, s);
 }
 
-int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
+// Number of schedule classes with work.
+int active_classes(const lb_handle* h)
 {
-    auto key = std::make_pair(len, parity);
-    auto it = h->graphs.find(key);
-    if (it != h->graphs.end()) {
-        *out = it->second;
+    int n = 0;
+    for (int c = 0; c < h->sched.n_class; ++c) n += h->cls_count[c] > 0;
+    return h->n_dom == 1 ? 0 : n;
+}
+
+// Enqueue `len` steps on `s` (the capture stream).  With several schedule
+// classes and chains on, each class runs its `len` launches as its own
+// chain on its own stream, forked from `s` at the start and joined back at
+// the end (the classes own disjoint domains).  fixed_parity: every step
+// reads the current buffer and writes the idle one (the state does not
+// advance; used to time candidates).
+int enqueue_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStream_t s)
+{
+    auto par = [&](int k) { return fixed_parity ? parity : parity ^ (k & 1); };
+    if (!(h->sched.chains && active_classes(h) > 1)) {
+        for (int k = 0; k < len; ++k) {
+            const int rc = enqueue_step(h, par(k), s);
+            if (rc != LB_OK) return rc;
+        }
         return LB_OK;
     }
+    LB_CUDA(cudaEventRecord(h->fork_ev, s));
+    int used = 0;
+    for (int c = 0; c < h->sched.n_class; ++c) {
+        if (h->cls_count[c] == 0) continue;
+        cudaStream_t sc = s;
+        if (used > 0) {
+            sc = h->chain[used - 1];
+            LB_CUDA(cudaStreamWaitEvent(sc, h->fork_ev, 0));
+        }
+        for (int k = 0; k < len; ++k) {
+            const int rc = launch_class(h, c, par(k), sc);
+            if (rc != LB_OK) return rc;
+        }
+        if (used > 0) LB_CUDA(cudaEventRecord(h->join_ev[used - 1], sc));
+        ++used;
+    }
+    for (int k = 0; k < len; ++k) {
+        const int rc = enqueue_geo(h, par(k), s);
+        if (rc != LB_OK) return rc;
+    }
+    for (int u = 1; u < used; ++u) LB_CUDA(cudaStreamWaitEvent(s, h->join_ev[u - 1], 0));
+    return LB_OK;
+}
+
+// Capture `len` steps into an executable graph.
+int capture_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaGraphExec_t* out)
+{
     cudaGraph_t graph = nullptr;
     LB_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = LB_OK;
-    for (int k = 0; k < len && rc == LB_OK; ++k) rc = enqueue_step(h, parity ^ (k & 1), h->cap_stream);
+    const int rc = enqueue_steps(h, len, parity, fixed_parity, h->cap_stream);
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
     if (rc != LB_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -313,6 +418,21 @@ int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess)
         return fail(LB_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+    *out = exec;
+    return LB_OK;
+}
+
+int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
+{
+    auto key = std::make_pair(len, parity);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return LB_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const int rc = capture_steps(h, len, parity, false, &exec);
+    if (rc != LB_OK) return rc;
     h->graphs[key] = exec;
     *out = exec;
     return LB_OK;
@@ -434,6 +554,14 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
             cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(fail(LB_ERR_CUDA, "device setup failed: %s", cudaGetErrorString(e)));
+    if (n_dom > 1) {
+        if ((e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(fail(LB_ERR_CUDA, "event setup failed: %s", cudaGetErrorString(e)));
+        for (int c = 0; c + 1 < LB_MAX_SCHED_CLASSES; ++c)
+            if ((e = cudaStreamCreateWithFlags(&h->chain[c], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->join_ev[c], cudaEventDisableTiming)) != cudaSuccess)
+                return bail(fail(LB_ERR_CUDA, "stream setup failed: %s", cudaGetErrorString(e)));
+    }
     if (dev_mem) {
         h->base = static_cast<unsigned char*>(dev_mem);
         h->owns = false;
@@ -505,10 +633,17 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
         return bail(fail(LB_ERR_CUDA, "device init failed: %s", cudaGetErrorString(e)));
     // default launch shape: 128 threads (64 with compact storage, whose
-    // threads take two columns each) x 32 rows (tuned by lb_autotune)
-    h->block_x = h->descs[0].compact ? 64 : 128;
-    h->rows = 32;
-    if (n_dom > 1) h->grid_persistent = h->sm_count * 8;
+    // threads take two columns each) x 32 rows, one class, a persistent grid
+    // of up to 8 CTAs per SM, items in domain order (tuned by lb_autotune)
+    h->sched.n_class = 1;
+    for (int c = 0; c < LB_MAX_SCHED_CLASSES; ++c) {
+        h->sched.max_nx[c] = 0;
+        h->sched.block_x[c] = h->descs[0].compact ? 64 : 128;
+        h->sched.rows[c] = 32;
+        h->sched.ctas_per_sm[c] = 8;
+    }
+    h->sched.order = 0;
+    h->sched.chains = 1;
     const int rc = build_items(h);
     if (rc != LB_OK) return bail(rc);
     *out = h;
@@ -679,6 +814,11 @@ void lb_destroy(lb_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     clear_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int c = 0; c + 1 < LB_MAX_SCHED_CLASSES; ++c) {
+        if (h->chain[c]) cudaStreamDestroy(h->chain[c]);
+        if (h->join_ev[c]) cudaEventDestroy(h->join_ev[c]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->owns && h->base) cudaFree(h->base);
     delete h;
 }
@@ -1222,23 +1362,142 @@ int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes)
 int lb_set_tile(lb_handle* h, int block_x, int rows)
 {
     if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
-    if (block_x < kMinBlockX || block_x > kMaxBlockX || block_x % 32 != 0 || rows < 1 ||
-        lbfe::step_smem_bytes(h->precision, block_x) == 0)
-        return fail(LB_ERR_INVALID_ARG, "block_x must be a multiple of 32 in [32, 256], rows >= 1");
-    LB_CUDA(cudaStreamSynchronize(h->stream));
-    clear_graphs(h);
-    h->block_x = block_x;
-    h->rows = rows;
-    return build_items(h);
+    lb_schedule sc = h->sched;
+    sc.n_class = 1;
+    sc.block_x[0] = block_x;
+    sc.rows[0] = rows;
+    return lb_set_schedule(h, &sc);
 }
 
 int lb_get_tile(const lb_handle* h, int* block_x, int* rows)
 {
     if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
-    if (block_x) *block_x = h->block_x;
-    if (rows) *rows = h->rows;
+    if (block_x) *block_x = h->block_x();
+    if (rows) *rows = h->rows();
     return LB_OK;
 }
+
+int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
+{
+    if (use_device(h) != LB_OK) return h ? LB_ERR_CUDA : LB_ERR_INVALID_ARG;
+    if (!sc) return fail(LB_ERR_INVALID_ARG, "schedule is NULL");
+    if (sc->n_class < 1 || sc->n_class > LB_MAX_SCHED_CLASSES)
+        return fail(LB_ERR_INVALID_ARG, "n_class must be in [1, %d]", LB_MAX_SCHED_CLASSES);
+    for (int c = 0; c < sc->n_class; ++c) {
+        const int bx = sc->block_x[c];
+        if (bx < kMinBlockX || bx > kMaxBlockX || bx % 32 != 0 || sc->rows[c] < 1 ||
+            lbfe::step_smem_bytes(h->precision, bx) == 0)
+            return fail(LB_ERR_INVALID_ARG,
+                        "block_x must be a multiple of 32 in [32, 256], rows >= 1 (class %d)", c);
+        if (sc->ctas_per_sm[c] < 0 || sc->ctas_per_sm[c] > 32)
+            return fail(LB_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 32] (class %d)", c);
+        if (c + 1 < sc->n_class &&
+            (sc->max_nx[c] < 1 || (c > 0 && sc->max_nx[c] <= sc->max_nx[c - 1])))
+            return fail(LB_ERR_INVALID_ARG, "max_nx must be positive and increasing");
+    }
+    if ((sc->order != 0 && sc->order != 1) || (sc->chains != 0 && sc->chains != 1))
+        return fail(LB_ERR_INVALID_ARG, "order and chains must be 0 or 1");
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    clear_graphs(h);
+    lb_schedule v = *sc;
+    for (int c = v.n_class; c < LB_MAX_SCHED_CLASSES; ++c) {  // unused classes: class 0's values
+        v.max_nx[c] = 0;
+        v.block_x[c] = v.block_x[0];
+        v.rows[c] = v.rows[0];
+        v.ctas_per_sm[c] = v.ctas_per_sm[0];
+    }
+    v.max_nx[v.n_class - 1] = 0;
+    h->sched = v;
+    return build_items(h);
+}
+
+int lb_get_schedule(const lb_handle* h, lb_schedule* sc)
+{
+    if (!h || !sc) return fail(LB_ERR_INVALID_ARG, "NULL argument");
+    *sc = h->sched;
+    return LB_OK;
+}
+
+namespace {
+
+// Device time per step of `len` fixed-parity steps (the state does not
+// advance), replayed `reps` times from a captured graph after one warm-up
+// replay.  Returns a negative value on failure (the error is recorded).
+double time_graph_steps(lb_handle* h, int len, int reps, cudaEvent_t e0, cudaEvent_t e1)
+{
+    cudaGraphExec_t g = nullptr;
+    if (capture_steps(h, len, h->parity, true, &g) != LB_OK) return -1.0;
+    double ms_step = -1.0;
+    if (cudaGraphLaunch(g, h->stream) == cudaSuccess && cudaEventRecord(e0, h->stream) == cudaSuccess) {
+        bool ok = true;
+        for (int k = 0; k < reps && ok; ++k) ok = cudaGraphLaunch(g, h->stream) == cudaSuccess;
+        float ms = 0.f;
+        if (ok && cudaEventRecord(e1, h->stream) == cudaSuccess &&
+            cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+            ms_step = double(ms) / (double(reps) * len);
+        else
+            fail(LB_ERR_CUDA, "autotune timing failed");
+    } else {
+        fail(LB_ERR_CUDA, "autotune launch failed");
+    }
+    cudaGraphExecDestroy(g);
+    h->launches += (long long)(reps + 1) * len * launches_per_step(h);
+    return ms_step;
+}
+
+// Candidate schedules of a batch: one class (every strip width, rows per
+// item, persistent or one-CTA-per-item grid, item order), and two size
+// classes (domains that fit one narrow strip, the rest wider), each class
+// with its own width, as independent chains, largest item first.
+std::vector<lb_schedule> batch_candidates(const lb_handle* h)
+{
+    const bool compact = h->descs[0].compact != 0;
+    std::vector<int> widths = compact ? std::vector<int>{64, 96, 128} : std::vector<int>{64, 128, 256};
+    if (h->precision == LB_FP64) widths = {64, 128};
+    const int rows_all[] = {16, 32, 64};
+    std::vector<lb_schedule> out;
+    auto base = [&]() {
+        lb_schedule s{};
+        s.n_class = 1;
+        s.chains = 1;
+        return s;
+    };
+    for (int bx : widths)
+        for (int r : rows_all)
+            for (int persistent = 0; persistent < 2; ++persistent)
+                for (int order = 0; order < 2; ++order) {
+                    lb_schedule s = base();
+                    s.block_x[0] = bx;
+                    s.rows[0] = r;
+                    s.ctas_per_sm[0] = persistent
+                        ? std::max(1, lbfe::step_batch_occupancy(h->precision, h->coll, compact, bx))
+                        : 0;
+                    s.order = order;
+                    out.push_back(s);
+                }
+    for (size_t a = 0; a < widths.size(); ++a)
+        for (size_t b = a + 1; b < widths.size(); ++b)
+            for (int r : {16, 32})
+                for (int persistent = 0; persistent < 2; ++persistent) {
+                    lb_schedule s = base();
+                    s.n_class = 2;
+                    const int bn = widths[a], bw = widths[b];
+                    s.max_nx[0] = compact ? lbfe::compact_strip(bn) : bn;
+                    s.block_x[0] = bn;
+                    s.block_x[1] = bw;
+                    s.rows[0] = s.rows[1] = r;
+                    for (int c = 0; c < 2; ++c)
+                        s.ctas_per_sm[c] = persistent
+                            ? std::max(1, lbfe::step_batch_occupancy(h->precision, h->coll, compact,
+                                                                     s.block_x[c]))
+                            : 0;
+                    s.order = 1;
+                    out.push_back(s);
+                }
+    return out;
+}
+
+}  // namespace
 
 int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms)
 {
@@ -1248,56 +1507,71 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
     // with obstacles only, no domain uses the staged kernel: nothing to tune
     const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
-    // compact storage: two columns per thread, so half the threads per strip
-    const int bxs_all[] = {64, 128, 256}, bxs_compact[] = {32, 64, 96, 128};
-    const int rws_all[] = {4, 8, 16, 32, 64, 128};
-    std::vector<int> bxs(bxs_all, bxs_all + 3), rws(rws_all, rws_all + 6);
-    if (h->descs[0].compact) bxs.assign(bxs_compact, bxs_compact + 4);
+    std::vector<lb_schedule> cands;
     if (!plain) {
-        bxs.assign(1, h->block_x);
-        rws.assign(1, h->rows);
+        cands.push_back(h->sched);
+    } else if (h->n_dom > 1) {
+        cands = batch_candidates(h);
+    } else {
+        // compact storage: two columns per thread, so half the threads per strip
+        const std::vector<int> bxs = h->descs[0].compact ? std::vector<int>{32, 64, 96, 128}
+                                                         : std::vector<int>{64, 128, 256};
+        const int rws[] = {4, 8, 16, 32, 64, 128};
+        for (int bx : bxs)
+            for (int r : rws) {
+                if (r > max_ny && r != rws[0]) continue;
+                lb_schedule s = h->sched;
+                s.n_class = 1;
+                s.block_x[0] = bx;
+                s.rows[0] = r;
+                cands.push_back(s);
+            }
     }
     cudaEvent_t e0, e1;
     LB_CUDA(cudaEventCreate(&e0));
     LB_CUDA(cudaEventCreate(&e1));
-    const int old_bx = h->block_x, old_rows = h->rows;
+    const lb_schedule old = h->sched;
     double best = 1e300;
-    int bb = old_bx, br = old_rows;
+    lb_schedule chosen = old;
     int rc = LB_OK;
-    for (int bx : bxs) {
-        for (int r : rws) {
-            if (r > max_ny && r != rws.front()) continue;
-            if ((rc = lb_set_tile(h, bx, r)) != LB_OK) break;
+    for (const lb_schedule& c : cands) {
+        if ((rc = lb_set_schedule(h, &c)) != LB_OK) break;
+        double ms;
+        if (h->n_dom > 1) {
+            // a few steps per graph, so that chains and tails show as they
+            // will in the step graphs
+            ms = time_graph_steps(h, 4, reps, e0, e1);
+        } else {
             // warm-up, then time `reps` launches that read the current buffer
             // and write the idle one (the state itself does not advance)
+            ms = -1.0;
             if ((rc = enqueue_step(h, h->parity, h->stream)) != LB_OK) break;
             cudaEventRecord(e0, h->stream);
             for (int k = 0; k < reps && rc == LB_OK; ++k) rc = enqueue_step(h, h->parity, h->stream);
             cudaEventRecord(e1, h->stream);
             if (rc != LB_OK) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = fail(LB_ERR_CUDA, "autotune timing failed");
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            float t = 0.f;
+            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+                ms = double(t) / reps;
             h->launches += (reps + 1) * launches_per_step(h);
-            if (ms / reps < best) {
-                best = ms / reps;
-                bb = bx;
-                br = r;
-            }
         }
-        if (rc != LB_OK) break;
+        if (ms < 0.0) {
+            rc = LB_ERR_CUDA;
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            chosen = c;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == LB_OK) rc = sync_and_check(h);
-    const int rc2 = lb_set_tile(h, rc == LB_OK ? bb : old_bx, rc == LB_OK ? br : old_rows);
+    const int rc2 = lb_set_schedule(h, rc == LB_OK ? &chosen : &old);
     if (rc != LB_OK) return rc;
     if (rc2 != LB_OK) return rc2;
-    if (block_x) *block_x = bb;
-    if (rows) *rows = br;
+    if (block_x) *block_x = h->block_x();
+    if (rows) *rows = h->rows();
     if (best_ms) *best_ms = best;
     return LB_OK;
 }

@@ -118,6 +118,12 @@ int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
 int prepare_step_f32();
 int prepare_step_f64();
 
+// Resident CTAs per SM of the batched step kernel for a launch shape (0 if
+// the shape is not supported or the query fails).
+int step_batch_occupancy(int precision, int coll, int compact, int block_x);
+int batch_occupancy_f32(int coll, int compact, int bx);
+int batch_occupancy_f64(int coll, int bx);
+
 // Dynamic shared memory of the step kernel for a block width (0 if the
 // width is not supported for this precision).
 size_t step_smem_bytes(int precision, int block_x);

@@ -40,6 +40,13 @@ int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_desc
                                  grid_persistent, sched, stream);
 }
 
+int step_batch_occupancy(int precision, int coll, int compact, int block_x)
+{
+    if (step_smem_bytes(precision, block_x) == 0) return 0;
+    return precision == 0 ? batch_occupancy_f32(coll, compact, block_x)
+                          : batch_occupancy_f64(coll, block_x);
+}
+
 // Periodic ghost columns of every row of the 18 planes of one buffer, from
 // the logical columns they mirror (used after host writes).
 template <typename Real>

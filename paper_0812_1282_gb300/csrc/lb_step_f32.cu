@@ -18,6 +18,12 @@ int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
                                    grid_p, sched, stream);
 }
 
+int batch_occupancy_f32(int coll, int compact, int bx)
+{
+    if (compact) return coll ? batch_occupancy_compact_w<true>(bx) : batch_occupancy_compact_w<false>(bx);
+    return coll ? batch_occupancy_w<float, true>(bx) : batch_occupancy_w<float, false>(bx);
+}
+
 int prepare_step_f32()
 {
     int e = prepare_step_prec<float>();

@@ -11,6 +11,11 @@ int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const Wo
                                     grid_p, sched, stream);
 }
 
+int batch_occupancy_f64(int coll, int bx)
+{
+    return coll ? batch_occupancy_w<double, true>(bx) : batch_occupancy_w<double, false>(bx);
+}
+
 int prepare_step_f64() { return prepare_step_prec<double>(); }
 
 }  // namespace lbfe

@@ -274,6 +274,53 @@ int launch_step_prec(int coll, const DomDesc& d, const DomDesc* d_descs, const W
                                                  rows, grid_p, sched, s));
 }
 
+// Resident CTAs per SM of the batched kernels for a launch shape (0 on error).
+template <bool MRT, int NWC>
+int batch_occupancy_compact_t(int bx)
+{
+    int n = 0;
+    const size_t smem = StageLayoutC(bx / 32, kStagesC).total();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_batch_compact_kernel<MRT, NWC>,
+                                                      bx + 32, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <typename Real, bool MRT, int NWC>
+int batch_occupancy_t(int bx)
+{
+    int n = 0;
+    const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_batch_kernel<Real, MRT, NWC>,
+                                                      bx + 32, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <bool MRT>
+int batch_occupancy_compact_w(int bx)
+{
+    switch (bx) {
+        case 32: return batch_occupancy_compact_t<MRT, 1>(bx);
+        case 64: return batch_occupancy_compact_t<MRT, 2>(bx);
+        case 96: return batch_occupancy_compact_t<MRT, 3>(bx);
+        case 128: return batch_occupancy_compact_t<MRT, 4>(bx);
+        case 256: return batch_occupancy_compact_t<MRT, 8>(bx);
+        default: return batch_occupancy_compact_t<MRT, 0>(bx);
+    }
+}
+
+template <typename Real, bool MRT>
+int batch_occupancy_w(int bx)
+{
+    switch (bx) {
+        case 64: return batch_occupancy_t<Real, MRT, 2>(bx);
+        case 128: return batch_occupancy_t<Real, MRT, 4>(bx);
+        case 256: return batch_occupancy_t<Real, MRT, 8>(bx);
+        default: return batch_occupancy_t<Real, MRT, 0>(bx);
+    }
+}
+
 template <bool MRT, int NWC>
 cudaError_t allow_large_smem_compact()
 {

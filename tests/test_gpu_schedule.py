@@ -1,0 +1,134 @@
+"""Batch schedules (lb_set_schedule, lb_autotune on a batch): how the work of
+one step is cut into classes, strips, row blocks and grids changes the
+launches, never the result.  Every schedule must give the state of the
+same domains stepped one by one, bit for bit, in both g storages; the
+autotuner must leave the state where it was."""
+import numpy as np
+import pytest
+
+import lbinputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0812_1282_gb300 as m
+
+    return m
+
+
+STEPS = 131  # a 64-step graph twice, a 2-step graph and one single step
+
+
+def _specs():
+    return lbinputs.batch_specs(n=10, seed=11, lo=40, hi=300)
+
+
+def _plist(lbf, specs, compact):
+    return [lbf.params(**lbinputs.BASE, collision="mrt", precision="fp32", compact_g=compact,
+                       tau_alpha=s["tau_alpha"], tau_beta=s["tau_beta"],
+                       h_bottom=lbf.lb_wetting_h(s["theta"]), step2_relax_momentum=True)
+            for s in specs]
+
+
+@pytest.fixture(scope="module", params=[False, True], ids=["full-g", "compact-g"])
+def single_states(lbf, request):
+    """Each domain stepped alone: the populations every schedule must give."""
+    compact = request.param
+    specs = _specs()
+    plist = _plist(lbf, specs, compact)
+    out = []
+    for d, s in enumerate(specs):
+        sim = lbf.Lattice(plist[d], s["nx"], s["ny"])
+        sim.init_drop(s["R"], s["cx"], s["cy"])
+        sim.step(STEPS)
+        out.append(sim.populations())
+        sim.close()
+    return compact, out
+
+
+def _schedules(lbf, compact):
+    w = (lambda bx: (62 * (bx // 32) - 2) // 4 * 4) if compact else (lambda bx: bx)
+    return {
+        "one-class-persistent": lbf.schedule(128, 32, ctas_per_sm=4),
+        "one-item-per-cta-largest-first": lbf.schedule(64, 16, ctas_per_sm=0, order=1),
+        "two-classes-chained": lbf.schedule([64, 128], [16, 32], ctas_per_sm=[0, 3],
+                                            max_nx=[w(64)], order=1),
+        "two-classes-in-turn": lbf.schedule([64, 128], 8, ctas_per_sm=[2, 0], max_nx=[w(64)],
+                                            chains=0),
+        "three-classes": lbf.schedule([64, 96, 128], [32, 5, 64], ctas_per_sm=[1, 0, 2],
+                                      max_nx=[100, 200], order=1),
+        "empty-class": lbf.schedule([64, 128], 32, max_nx=[10]),
+    }
+
+
+@pytest.mark.parametrize("name", ["one-class-persistent", "one-item-per-cta-largest-first",
+                                  "two-classes-chained", "two-classes-in-turn", "three-classes",
+                                  "empty-class"])
+def test_schedule_gives_single_domain_results(lbf, single_states, name):
+    compact, ref = single_states
+    specs = _specs()
+    plist = _plist(lbf, specs, compact)
+    batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
+    batch.set_schedule(_schedules(lbf, compact)[name])
+    got = batch.schedule()
+    assert got["n_class"] == _schedules(lbf, compact)[name].n_class
+    for d, s in enumerate(specs):
+        batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    batch.step(STEPS)
+    for d in range(len(specs)):
+        fb, gb = batch.populations(dom=d)
+        assert np.array_equal(fb, ref[d][0]) and np.array_equal(gb, ref[d][1]), (name, d)
+    batch.close()
+
+
+def test_autotune_keeps_state_and_picks_valid_schedule(lbf):
+    specs = _specs()
+    plist = _plist(lbf, specs, True)
+    batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
+    for d, s in enumerate(specs):
+        batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    batch.step(7)
+    before = batch.save_state()
+    bx, rows, ms = batch.autotune(reps=1)
+    assert batch.save_state() == before
+    sc = batch.schedule()
+    assert sc["block_x"][0] == bx and sc["rows"][0] == rows and ms > 0
+    assert 1 <= sc["n_class"] <= 2 and sc["order"] in (0, 1)
+    # and stepping on with the chosen schedule still matches a fresh run
+    batch.step(20)
+    other = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
+    for d, s in enumerate(specs):
+        other.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+    other.step(27)
+    assert other.save_state()[32:] == batch.save_state()[32:]
+    batch.close()
+    other.close()
+
+
+def test_schedule_validation(lbf):
+    specs = _specs()[:3]
+    plist = _plist(lbf, specs, True)
+    batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
+    bad = [lbf.schedule(48, 32),                                  # not a multiple of 32
+           lbf.schedule(128, 0),                                  # no rows
+           lbf.schedule(128, 32, ctas_per_sm=33),                 # too many CTAs per SM
+           lbf.schedule([64, 128, 128], 32, max_nx=[200, 100]),   # limits not increasing
+           lbf.schedule(128, 32, order=2)]
+    for sc in bad:
+        with pytest.raises(lbf.LBError) as e:
+            batch.set_schedule(sc)
+        assert e.value.code == lbf.LB_ERR_INVALID_ARG
+    sc = lbf.Schedule()
+    sc.n_class = 5
+    with pytest.raises(lbf.LBError):
+        batch.set_schedule(sc)
+    batch.close()
