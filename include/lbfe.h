@@ -267,7 +267,8 @@ int lb_save_state(lb_handle* h, void* host_buf, size_t bytes);
 int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes);
 
 /* Launch shape: threads per CTA along x (block_x, a multiple of 32 in
- * [32, 256]) and rows each CTA marches through (rows >= 1).  Results do not
+ * [32, 256], or [32, 288] with compact g storage) and rows each CTA marches
+ * through (rows >= 1).  Results do not
  * depend on it.  On a batch it sets a one-class schedule with that shape
  * (lb_schedule).  Invalidates captured graphs. */
 int lb_set_tile(lb_handle* h, int block_x, int rows);
@@ -299,7 +300,7 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
  * Errors: LB_ERR_INVALID_ARG for a value out of range or max_nx not
  * increasing. */
-#define LB_MAX_SCHED_CLASSES 4
+#define LB_MAX_SCHED_CLASSES 8
 typedef struct lb_schedule {
     int n_class;
     int max_nx[LB_MAX_SCHED_CLASSES];

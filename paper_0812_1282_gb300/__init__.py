@@ -41,7 +41,7 @@ EXPORTS = (
     "lb_init_channel", "lb_meniscus", "lb_set_wetting", "lb_set_schedule", "lb_get_schedule",
     "lb_fp64_peak",
 )
-LB_MAX_SCHED_CLASSES = 4
+LB_MAX_SCHED_CLASSES = 8
 
 
 class LBError(RuntimeError):

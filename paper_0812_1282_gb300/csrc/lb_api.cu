@@ -44,6 +44,7 @@ int fail(int code, const char* fmt, ...)
 constexpr size_t kAlign = 256;
 constexpr int kMinBlockX = 32;
 constexpr int kMaxBlockX = 256;
+constexpr int kMaxBlockXCompact = 288;
 constexpr int kGraphBig = 64;
 constexpr int kGraphSmall = 2;
 constexpr int kChunk = 1 << 20;  // nodes per staging chunk for host field output
@@ -190,6 +191,11 @@ struct lb_handle {
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[LB_MAX_SCHED_CLASSES - 1] = {nullptr};
     int n_items = 0;
+    // compact g storage: a strip that covers its whole domain takes the
+    // periodic wrap from its own stage copy and leaves the ghost columns
+    // alone, so after steps they may be stale; they are refreshed before
+    // another schedule (which may split a domain) or a checkpoint uses them
+    bool ghosts_stale = false;
     int parity = 0;
     long long steps = 0;
     long long launches = 0;
@@ -435,6 +441,22 @@ int get_graph(lb_handle* h, int len, int parity, cudaGraphExec_t* out)
     if (rc != LB_OK) return rc;
     h->graphs[key] = exec;
     *out = exec;
+    return LB_OK;
+}
+
+// Rewrite the periodic ghost columns of every domain's current buffer from
+// the columns they copy (see lb_handle::ghosts_stale).
+int refresh_ghosts(lb_handle* h)
+{
+    if (!h->ghosts_stale) return LB_OK;
+    for (const DomDesc& D : h->descs) {
+        if (D.cls) continue;
+        const int e = lbfe::launch_fill_ghosts(h->precision, D, h->parity, h->stream);
+        if (e != 0) return fail(LB_ERR_CUDA, "ghost refresh failed: %s", cudaGetErrorString(cudaError_t(e)));
+        h->launches += 1;
+    }
+    LB_CUDA(cudaStreamSynchronize(h->stream));
+    h->ghosts_stale = false;
     return LB_OK;
 }
 
@@ -878,6 +900,7 @@ int lb_step(lb_handle* h, int n)
     if (!h) return fail(LB_ERR_INVALID_ARG, "handle is NULL");
     if (n < 0) return fail(LB_ERR_INVALID_ARG, "n must be >= 0");
     if (use_device(h) != LB_OK) return LB_ERR_CUDA;
+    if (n > 0 && h->descs[0].compact) h->ghosts_stale = true;
     while (n > 0) {
         int len = n >= kGraphBig ? kGraphBig : (n >= kGraphSmall ? kGraphSmall : 1);
         if (len == 1) {
@@ -1321,6 +1344,8 @@ int lb_save_state(lb_handle* h, void* host_buf, size_t bytes)
     if (!h || !host_buf) return fail(LB_ERR_INVALID_ARG, "NULL argument");
     if (use_device(h) != LB_OK) return LB_ERR_CUDA;
     if (bytes < lb_state_bytes(h)) return fail(LB_ERR_INVALID_ARG, "buffer too small");
+    const int rg = refresh_ghosts(h);  // the saved state holds current ghost columns
+    if (rg != LB_OK) return rg;
     long long* hdr = static_cast<long long*>(host_buf);
     hdr[0] = 0x4c4246454348LL;  // magic
     hdr[1] = h->n_dom;
@@ -1356,6 +1381,7 @@ int lb_load_state(lb_handle* h, const void* host_buf, size_t bytes)
     }
     LB_CUDA(cudaStreamSynchronize(h->stream));
     h->steps = hdr[3];
+    h->ghosts_stale = false;
     return LB_OK;
 }
 
@@ -1385,10 +1411,13 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
         return fail(LB_ERR_INVALID_ARG, "n_class must be in [1, %d]", LB_MAX_SCHED_CLASSES);
     for (int c = 0; c < sc->n_class; ++c) {
         const int bx = sc->block_x[c];
-        if (bx < kMinBlockX || bx > kMaxBlockX || bx % 32 != 0 || sc->rows[c] < 1 ||
-            lbfe::step_smem_bytes(h->precision, bx) == 0)
+        // compact storage takes strips of up to nine compute warps (556 columns)
+        const int max_bx = h->descs[0].compact ? kMaxBlockXCompact : kMaxBlockX;
+        if (bx < kMinBlockX || bx > max_bx || bx % 32 != 0 || sc->rows[c] < 1 ||
+            (!h->descs[0].compact && lbfe::step_smem_bytes(h->precision, bx) == 0))
             return fail(LB_ERR_INVALID_ARG,
-                        "block_x must be a multiple of 32 in [32, 256], rows >= 1 (class %d)", c);
+                        "block_x must be a multiple of 32 in [32, %d], rows >= 1 (class %d)", max_bx,
+                        c);
         if (sc->ctas_per_sm[c] < 0 || sc->ctas_per_sm[c] > 32)
             return fail(LB_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 32] (class %d)", c);
         if (c + 1 < sc->n_class &&
@@ -1397,6 +1426,8 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
     }
     if ((sc->order != 0 && sc->order != 1) || (sc->chains != 0 && sc->chains != 1))
         return fail(LB_ERR_INVALID_ARG, "order and chains must be 0 or 1");
+    const int rg = refresh_ghosts(h);  // the new schedule may split a domain into strips
+    if (rg != LB_OK) return rg;
     LB_CUDA(cudaStreamSynchronize(h->stream));
     clear_graphs(h);
     lb_schedule v = *sc;
@@ -1445,55 +1476,60 @@ double time_graph_steps(lb_handle* h, int len, int reps, cudaEvent_t e0, cudaEve
     return ms_step;
 }
 
-// Candidate schedules of a batch: one class (every strip width, rows per
-// item, persistent or one-CTA-per-item grid, item order), and two size
-// classes (domains that fit one narrow strip, the rest wider), each class
-// with its own width, as independent chains, largest item first.
+// Candidate schedules of a batch.
+//  - One class: every strip width, rows per item, a persistent or one-CTA-
+//    per-item grid, and the item order.
+//  - Ladders of size classes: a class per strip width, each taking the
+//    domains that fit one of its strips (so that with compact storage a
+//    domain is one strip, which wraps in shared memory and writes no ghost
+//    columns), as independent chains, largest item first, with taller
+//    items (fewer halo rows per node).
 std::vector<lb_schedule> batch_candidates(const lb_handle* h)
 {
     const bool compact = h->descs[0].compact != 0;
     std::vector<int> widths = compact ? std::vector<int>{64, 96, 128} : std::vector<int>{64, 128, 256};
     if (h->precision == LB_FP64) widths = {64, 128};
-    const int rows_all[] = {16, 32, 64};
     std::vector<lb_schedule> out;
-    auto base = [&]() {
-        lb_schedule s{};
-        s.n_class = 1;
-        s.chains = 1;
-        return s;
+    auto occ = [&](int bx) {
+        return std::max(1, lbfe::step_batch_occupancy(h->precision, h->coll, compact, bx));
     };
     for (int bx : widths)
-        for (int r : rows_all)
+        for (int r : {16, 32, 64})
             for (int persistent = 0; persistent < 2; ++persistent)
                 for (int order = 0; order < 2; ++order) {
-                    lb_schedule s = base();
+                    lb_schedule s{};
+                    s.n_class = 1;
+                    s.chains = 1;
                     s.block_x[0] = bx;
                     s.rows[0] = r;
-                    s.ctas_per_sm[0] = persistent
-                        ? std::max(1, lbfe::step_batch_occupancy(h->precision, h->coll, compact, bx))
-                        : 0;
+                    s.ctas_per_sm[0] = persistent ? occ(bx) : 0;
                     s.order = order;
                     out.push_back(s);
                 }
-    for (size_t a = 0; a < widths.size(); ++a)
-        for (size_t b = a + 1; b < widths.size(); ++b)
-            for (int r : {16, 32})
-                for (int persistent = 0; persistent < 2; ++persistent) {
-                    lb_schedule s = base();
-                    s.n_class = 2;
-                    const int bn = widths[a], bw = widths[b];
-                    s.max_nx[0] = compact ? lbfe::compact_strip(bn) : bn;
-                    s.block_x[0] = bn;
-                    s.block_x[1] = bw;
-                    s.rows[0] = s.rows[1] = r;
-                    for (int c = 0; c < 2; ++c)
-                        s.ctas_per_sm[c] = persistent
-                            ? std::max(1, lbfe::step_batch_occupancy(h->precision, h->coll, compact,
-                                                                     s.block_x[c]))
-                            : 0;
-                    s.order = 1;
-                    out.push_back(s);
-                }
+    std::vector<std::vector<int>> ladders;
+    if (compact)
+        ladders = {{96, 160, 224, 288},
+                   {96, 160, 192, 224, 288},
+                   {96, 128, 160, 192, 224, 256, 288},
+                   {64, 96, 128, 160, 192, 224, 256, 288}};
+    else if (h->precision == LB_FP32)
+        ladders = {{64, 128, 256}, {64, 128, 192, 256}};
+    else
+        ladders = {{64, 128}};
+    for (const auto& lad : ladders)
+        for (int r : {32, 64, 96, 128}) {
+            lb_schedule s{};
+            s.n_class = int(lad.size());
+            s.chains = 1;
+            s.order = 1;
+            for (int c = 0; c < s.n_class; ++c) {
+                s.block_x[c] = lad[c];
+                s.rows[c] = r;
+                s.ctas_per_sm[c] = 0;
+                s.max_nx[c] = compact ? lbfe::compact_strip(lad[c]) : lad[c];
+            }
+            out.push_back(s);
+        }
     return out;
 }
 

@@ -32,7 +32,9 @@ int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_desc
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x, int rows,
                 int grid_persistent, int* sched, void* stream)
 {
-    if (step_smem_bytes(precision, block_x) == 0) return int(cudaErrorInvalidValue);
+    const bool ok = d.compact ? (block_x >= 32 && block_x <= 288 && block_x % 32 == 0)
+                              : step_smem_bytes(precision, block_x) != 0;
+    if (!ok) return int(cudaErrorInvalidValue);
     return precision == 0
                ? launch_step_f32(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
                                  grid_persistent, sched, stream)
@@ -42,7 +44,8 @@ int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_desc
 
 int step_batch_occupancy(int precision, int coll, int compact, int block_x)
 {
-    if (step_smem_bytes(precision, block_x) == 0) return 0;
+    if (compact ? (block_x < 32 || block_x > 288 || block_x % 32) : step_smem_bytes(precision, block_x) == 0)
+        return 0;
     return precision == 0 ? batch_occupancy_f32(coll, compact, block_x)
                           : batch_occupancy_f64(coll, block_x);
 }

@@ -190,10 +190,11 @@ __device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<
 // Compute warp cw of NW.  Its lane expands columns je, je + 1 (je = 62 cw +
 // 2 lane; strip column j is lattice column x0 - 2 + j) and collides nodes
 // jn, jn + 1 (jn = 2 (32 cw + lane); node n is lattice column x0 + n).  The
-// phi and word rings are indexed by strip column j.  prm_shared, when set,
-// holds the node parameters in shared memory; the collision then reads them
-// at each use instead of keeping them in registers for the whole tile.
-template <bool MRT, int S, int NWC = 0>
+// phi and word rings are indexed by strip column j.  With PRM_SMEM the node
+// parameters (and the wall wetting gradients) come from prm_shared, a copy
+// in shared memory read at each use, instead of registers held for the
+// whole tile (the batched form, whose parameters change from tile to tile).
+template <bool MRT, int S, int NWC = 0, bool PRM_SMEM = false>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
                                                int nw, int cw, unsigned& q,
@@ -224,6 +225,23 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const int ncols = cols > 0 ? cols : min(L.W, nx - x0);  // node columns of this strip
     const bool n_on = jn < ncols;
     const int x = x0 + jn;
+    // A strip that covers its whole domain takes the periodic wrap from its
+    // own stage copy: lattice column c < 0 or c >= nx is read at stage
+    // index (c mod nx) + 4 instead of the ghost columns, which such a strip
+    // therefore neither reads nor writes.  Only the few lanes whose columns
+    // wrap do anything extra.  Expansion lane: columns je - 2, je - 1 of the
+    // domain (stage indices ex0, ex1); collision lane: pulls across x = 0 or
+    // x = nx - 1.
+    // One bit mask keeps the lane's wrap cases (the indices are recomputed
+    // on the rare path): 1 expansion columns wrap, 2 node jn pulls from
+    // x = -1, 4 node jn pulls from x = nx, 8 node jn + 1 pulls from x = nx.
+    const bool whole = x0 == 0 && ncols == nx;
+    auto wrap_idx = [nx](int c) { return (c < 0 ? c + nx : (c >= nx ? c - nx : c)) + 4; };
+    const unsigned wrapbits =
+        whole ? (unsigned(wrap_idx(je - 2) != je + 2 || wrap_idx(je - 1) != je + 3) |
+                 (unsigned(jn == 0) << 1) | (unsigned(jn + 1 == nx) << 2) |
+                 (unsigned(jn + 2 == nx) << 3))
+              : 0u;
 
     auto slot_of = [&](int p) { return (qb + unsigned(p)) % unsigned(S); };
     auto stage_ptr = [&](int p) { return stage + size_t(slot_of(p)) * L.stage_elems(); };
@@ -264,10 +282,18 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
         if (has_c) {
             // 1. expand (every lane: all take part in the shuffles)
             const float* sc = stage_ptr(p) + 9 * segw + je + 2;
-            wd_q = ld_pair(sc);
+            float2 cv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cv[k] = ld_pair(sc + k * segw);
+            if (wrapbits & 1u) {
+                const float* sw = stage_ptr(p) + 9 * segw;
+                const int ex0 = wrap_idx(je - 2), ex1 = wrap_idx(je - 1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cv[k] = make_float2(sw[k * segw + ex0], sw[k * segw + ex1]);
+            }
+            wd_q = f2(cv[0]);
             f2 ge[9];
-            g_equilibria2(g0_value2(wd_q), ld_pair(sc + segw), ld_pair(sc + 2 * segw),
-                          ld_pair(sc + 3 * segw), ge);
+            g_equilibria2(g0_value2(wd_q), f2(cv[1]), f2(cv[2]), f2(cv[3]), ge);
             tl_q = g_tail_sum2(ge);
             // 2. what enters column je from the left and je + 1 from the right
             const f2 g5l(__shfl_up_sync(kAll, ge[5].v.y, 1), ge[5].v.x);
@@ -323,6 +349,27 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             fi[6] = bhi ? ld_pair(sb + 6 * segw) : ld_two(sb + 6 * segw + 1);
             fi[7] = blo ? ld_pair(sb + 7 * segw) : ld_two(sb + 7 * segw + 1);
             fi[8] = bhi ? ld_pair(sb + 8 * segw) : ld_two(sb + 8 * segw - 1);
+            if (wrapbits & 14u) {
+                // whole-domain strip: pulls across the periodic boundary read
+                // the stage copy at the wrapped column (stage index nx + 3 for
+                // x = -1, 4 for x = nx)
+                const float* st = stage_ptr(p);
+                if (wrapbits & 2u) {
+                    fi[1].v.x = st[segw + nx + 3];
+                    if (!blo) fi[5].v.x = st[5 * segw + nx + 3];
+                    if (!bhi) fi[8].v.x = st[8 * segw + nx + 3];
+                }
+                if (wrapbits & 4u) {
+                    fi[2].v.x = st[2 * segw + 4];
+                    if (!bhi) fi[6].v.x = st[6 * segw + 4];
+                    if (!blo) fi[7].v.x = st[7 * segw + 4];
+                }
+                if (wrapbits & 8u) {
+                    fi[2].v.y = st[2 * segw + 4];
+                    if (!bhi) fi[6].v.y = st[6 * segw + 4];
+                    if (!blo) fi[7].v.y = st[7 * segw + 4];
+                }
+            }
             // phi of strip columns jn + 1 .. jn + 4 of rows y - 1, y, y + 1
             // (centres jn + 2, jn + 3); a wall ghost row is row k - 1 (or
             // ny - k) less k h: the mirror (k = 2) or one-sided (k = 1) rule
@@ -337,7 +384,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             row3(rslot(y), cw_, cc, ce);
             if (bhi) {
                 row3(rslot(ny - D.wet_k), nw_, nc, ne);
-                const f2 h(float(D.wet_k) * prm.h_top);
+                const f2 h(float(D.wet_k) * (PRM_SMEM ? prm_shared->h_top : prm.h_top));
                 nw_ = nw_ - h;
                 nc = nc - h;
                 ne = ne - h;
@@ -346,7 +393,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             }
             if (blo) {
                 row3(rslot(D.wet_k - 1), sw, sc_, se);
-                const f2 h(float(D.wet_k) * prm.h_bot);
+                const f2 h(float(D.wet_k) * (PRM_SMEM ? prm_shared->h_bot : prm.h_bot));
                 sw = sw - h;
                 sc_ = sc_ - h;
                 se = se - h;
@@ -357,7 +404,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             stencils2(cc, ce, cw_, nc, sc_, ne, nw_, se, sw, dx, dy, lap);
             const bool s2 = D.step2 && (blo || bhi);
             f2 fo2[9], uxe, uye, gmu;
-            if (prm_shared) {
+            if constexpr (PRM_SMEM) {
                 const volatile NodeParams<float>& PV = *prm_shared;
                 collide_f2<MRT>(PV, fi, cc, dx, dy, lap, s2, D.step2_relax_j != 0, fo2, uxe, uye);
                 gmu = gamma_mu2(PV, cc, lap);
@@ -379,9 +426,11 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
                 for (int kk = 0; kk < 4; ++kk) cd[kk * P + o] = co2[kk].v.x;
             }
             // periodic ghost copies: logical 0, 1 also at nx, nx+1 and
-            // logical nx-2, nx-1 also at -2, -1
+            // logical nx-2, nx-1 also at -2, -1 (a whole-domain strip wraps
+            // in its stage copy instead)
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
+                if (whole) break;
                 const int xl = x + l;
                 if (jn + l >= ncols) continue;
                 if (xl < 2) {

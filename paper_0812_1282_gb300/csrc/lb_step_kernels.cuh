@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
 // Compact-g forms (FP32, tau_phi = 1; lb_step_compact.cuh).  Same launch
 // shapes and scheduling as above, with strips of compact_strip(bx) columns.
 template <bool MRT, int NWC>
-__global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int parity, int rows)
+__global__ void __launch_bounds__(320) step_single_compact_kernel(DomDesc D, int parity, int rows)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStagesC;
@@ -123,8 +123,12 @@ __global__ void __launch_bounds__(288) step_single_compact_kernel(DomDesc D, int
     }
 }
 
+// Register budget of the batched compact kernel: 96 registers per thread,
+// so that as many CTAs fit an SM as their shared memory allows (four of
+// NW = 4).
 template <bool MRT, int NWC>
-__global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* __restrict__ descs,
+__global__ void __maxnreg__(96)
+    step_batch_compact_kernel(const DomDesc* __restrict__ descs,
                                                                  const WorkItem* __restrict__ items,
                                                                  int n_items, int parity,
                                                                  int* sched, unsigned* err)
@@ -132,6 +136,7 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int tags[kStagesC];
     __shared__ NodeParams<float> tile_prm;  // the current tile's node parameters
+    __shared__ DomDesc tile_desc;           // and its domain (compute warps)
     constexpr int S = kStagesC;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages_c<S>(smem, NW);
@@ -166,13 +171,16 @@ __global__ void __launch_bounds__(288) step_batch_compact_kernel(const DomDesc* 
             // them stops all), so that they meet at the same barriers
             if (named_sync_or(kComputeBarrier, 32 * NW, it < 0 || it >= n_items)) break;
             const WorkItem w = items[it];
-            const DomDesc D = descs[w.dom];
             // every compute warp is past the previous tile: refresh the shared
-            // copy of the node parameters, which the collision reads at each use
-            if (warp == 1 && lane == 0) tile_prm = node_params<float>(D);
+            // copies of the domain descriptor and its node parameters, which
+            // the tile reads at each use instead of holding them in registers
+            if (warp == 1 && lane == 0) {
+                tile_desc = descs[w.dom];
+                tile_prm = node_params<float>(tile_desc);
+            }
             named_sync(kComputeBarrier, 32 * NW);
-            consume_tile_c<MRT, S, NWC>(D, parity, w.x0, w.y0, w.rows, w.cols, smem, NW,
-                                        warp - 1, q, &tile_prm);
+            consume_tile_c<MRT, S, NWC, true>(tile_desc, parity, w.x0, w.y0, w.rows, w.cols, smem,
+                                              NW, warp - 1, q, &tile_prm);
         }
     }
 }
