@@ -398,7 +398,7 @@ def run_capillary(lbf, torch, steps=None):
                 l_final=float(l[-1]), theta_a_late=theta_a,
                 washburn_slope=slope, washburn_slope_theory=k_theory,
                 nonfinite=int(st["nonfinite"]),
-                note="obstacle path, two launches per step; front by lb_meniscus every 500 "
+                note="obstacle path, one fused launch per step; front by lb_meniscus every 500 "
                      "steps; Washburn fit (nu_a - nu_b) l^2/2 + nu_b L l vs t over the second "
                      "half, theory gamma w cos(theta_a) / 6")
 

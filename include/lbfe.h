@@ -196,7 +196,7 @@ int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
  * (params.walls) stay solid rows with h_bottom / h_top.  Solid nodes hold
  * the rest state and report rho = phi = u = 0; they are left out of the
  * statistics and of the interface points.  A domain with obstacles is
- * stepped by two plain kernels per step instead of the staged one.
+ * stepped by one plain kernel per step instead of the staged one.
  * The state must be initialised again afterwards (lb_init_*).
  * Errors: LB_ERR_INVALID_ARG for a class out of range or without a
  * gradient, a non-finite gradient, a map without fluid, or a solid node

@@ -67,8 +67,7 @@ int pitch_for(int nx, int precision)
 struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
-    std::vector<size_t> geo_off;    // domain d's obstacle map (nx*ny bytes), then its phi field
-    std::vector<size_t> geo_phi;    // offset of domain d's phi field
+    std::vector<size_t> geo_off;    // domain d's obstacle map (nx*ny bytes)
     size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0,
            sched = 0;
     size_t total = 0;
@@ -92,12 +91,10 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
         L.dom_off.push_back(off);
         L.dom_bytes.push_back(buf);
         off += 2 * buf;
-        // room for an obstacle map and the per-node phi of the obstacle step
+        // room for an obstacle map
         const size_t nodes = size_t(nx[d]) * size_t(ny[d]);
         L.geo_off.push_back(off);
         off = align_up(off + nodes, kAlign);
-        L.geo_phi.push_back(off);
-        off = align_up(off + nodes * es, kAlign);
         max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
         max_nx = std::max<long long>(max_nx, nx[d]);
         // at most ceil(nx / 28) strips per row (the narrowest strip of any
@@ -320,7 +317,7 @@ long long launches_per_step(const lb_handle* h)
         n = h->descs[0].cls == nullptr ? 1 : 0;
     else
         for (int c = 0; c < h->sched.n_class; ++c) n += h->cls_count[c] > 0;
-    return n + 2LL * h->n_geo;
+    return n + h->n_geo;  // one launch per domain with obstacles
 }
 
 int enqueue_geo(lb_handle* h, int parity, cudaStream_t s)
@@ -338,7 +335,7 @@ int enqueue_geo(lb_handle* h, int parity, cudaStream_t s)
 
 // One time step of every domain: the staged kernel for the domains without
 // obstacles (one launch for a single domain; one per schedule class for a
-// batch, one after the other), then two launches per domain with obstacles.
+// batch, one after the other), then one launch per domain with obstacles.
 int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
 {
     if (h->n_dom == 1) {
@@ -642,7 +639,6 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         D.flut_inv = float(D.lut_inv);
         D.flut_kmax = float(D.lut_kmax);
         D.cls = nullptr;
-        D.phi = h->base + L.geo_phi[d];
         for (int k = 0; k < 8; ++k) {
             D.hcls[k] = 0.0;
             D.fhcls[k] = 0.0f;
@@ -1517,7 +1513,7 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
     else
         ladders = {{64, 128}};
     for (const auto& lad : ladders)
-        for (int r : {32, 64, 96, 128}) {
+        for (int r : {48, 64, 96, 128}) {
             lb_schedule s{};
             s.n_class = int(lad.size());
             s.chains = 1;
@@ -1549,9 +1545,12 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     } else if (h->n_dom > 1) {
         cands = batch_candidates(h);
     } else {
-        // compact storage: two columns per thread, so half the threads per strip
-        const std::vector<int> bxs = h->descs[0].compact ? std::vector<int>{32, 64, 96, 128}
-                                                         : std::vector<int>{64, 128, 256};
+        // compact storage: two columns per thread, so half the threads per
+        // strip, and strips up to nine compute warps wide (a domain that fits
+        // one strip wraps in shared memory)
+        const std::vector<int> bxs =
+            h->descs[0].compact ? std::vector<int>{32, 64, 96, 128, 160, 192, 224, 256, 288}
+                                : std::vector<int>{64, 128, 256};
         const int rws[] = {4, 8, 16, 32, 64, 128};
         for (int bx : bxs)
             for (int r : rws) {
@@ -1570,36 +1569,53 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     double best = 1e300;
     lb_schedule chosen = old;
     int rc = LB_OK;
-    for (const lb_schedule& c : cands) {
-        if ((rc = lb_set_schedule(h, &c)) != LB_OK) break;
-        double ms;
-        if (h->n_dom > 1) {
-            // a few steps per graph, so that chains and tails show as they
-            // will in the step graphs
-            ms = time_graph_steps(h, 4, reps, e0, e1);
-        } else {
-            // warm-up, then time `reps` launches that read the current buffer
-            // and write the idle one (the state itself does not advance)
-            ms = -1.0;
-            if ((rc = enqueue_step(h, h->parity, h->stream)) != LB_OK) break;
-            cudaEventRecord(e0, h->stream);
-            for (int k = 0; k < reps && rc == LB_OK; ++k) rc = enqueue_step(h, h->parity, h->stream);
-            cudaEventRecord(e1, h->stream);
-            if (rc != LB_OK) break;
-            float t = 0.f;
-            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
-                ms = double(t) / reps;
-            h->launches += (reps + 1) * launches_per_step(h);
-        }
+    // one timing of a candidate (ms per step); negative on failure
+    auto time_candidate = [&](const lb_schedule& c, int len, int r) -> double {
+        if ((rc = lb_set_schedule(h, &c)) != LB_OK) return -1.0;
+        if (h->n_dom > 1) return time_graph_steps(h, len, r, e0, e1);
+        // warm-up, then time `r` launches that read the current buffer and
+        // write the idle one (the state itself does not advance)
+        if ((rc = enqueue_step(h, h->parity, h->stream)) != LB_OK) return -1.0;
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < r && rc == LB_OK; ++k) rc = enqueue_step(h, h->parity, h->stream);
+        cudaEventRecord(e1, h->stream);
+        if (rc != LB_OK) return -1.0;
+        float t = 0.f;
+        h->launches += (r + 1) * launches_per_step(h);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return -1.0;
+        return double(t) / r;
+    };
+    // a batch: a few steps per graph, so that chains and tails show as they
+    // will in the step graphs; then the fastest few again over longer graphs
+    // (the short timings of neighbouring candidates are within noise)
+    std::vector<std::pair<double, size_t>> scored;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        const double ms = time_candidate(cands[k], 4, reps);
         if (ms < 0.0) {
-            rc = LB_ERR_CUDA;
+            if (rc == LB_OK) rc = LB_ERR_CUDA;
             break;
         }
-        if (ms < best) {
-            best = ms;
-            chosen = c;
-        }
+        scored.emplace_back(ms, k);
     }
+    if (rc == LB_OK && h->n_dom > 1 && scored.size() > 1) {
+        std::sort(scored.begin(), scored.end());
+        const size_t top = std::min<size_t>(6, scored.size());
+        for (size_t t = 0; t < top && rc == LB_OK; ++t) {
+            const double ms = time_candidate(cands[scored[t].second], 16, reps + 2);
+            if (ms < 0.0) {
+                if (rc == LB_OK) rc = LB_ERR_CUDA;
+                break;
+            }
+            scored[t].first = ms;
+        }
+        scored.resize(top);
+    }
+    for (const auto& sc : scored)
+        if (sc.first < best) {
+            best = sc.first;
+            chosen = cands[sc.second];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == LB_OK) rc = sync_and_check(h);

@@ -16,17 +16,26 @@
 //     plain step, so both paths agree there.
 // With walls, the rows y = -1 and y = ny are solid with h_bot / h_top.
 //
-// A step is two launches on one thread per node: the first forms phi of
-// every fluid node from its pulled g (Eq. moments) into a per-node field,
-// the second pulls f and g again, takes the phi stencil from that field
-// (ghost values at solid neighbours), collides (the node arithmetic of the
-// plain step) and stores.  Solid nodes are never written by a step; they
-// hold the rest state (f = t, g = 0), so they carry no fluid.
+// A step is one launch.  A CTA owns a tile of kGTX x kGTY nodes (one per
+// thread) and, in shared memory:
+//   1. the class map of the tile and a kGC-node halo;
+//   2. phi of the tile and a kGH-node halo, each fluid node's sum of its
+//      pulled g (Eq. moments): a ghost value at a solid neighbour reads phi
+//      up to three nodes from the fluid node it serves (the solid node, then
+//      twice the direction towards fluid), and the pulls of the halo reach
+//      one node further;
+// then each fluid node of the tile pulls f and g, takes the phi stencil
+// from shared memory (ghost values at solid neighbours), collides (the node
+// arithmetic of the plain step) and stores.  Halo nodes are formed by
+// several CTAs with the same arithmetic, so every tile sees the same phi.
+// Solid nodes are never written by a step; they hold the rest state
+// (f = t, g = 0), so they carry no fluid.
 //
 // The obstacle path serves small and medium geometries (the capillary set-up
-// is ~10^5 nodes), where a step is bound by launch latency rather than by
-// HBM bandwidth, so it uses plain coalesced loads instead of the staged
-// pipeline of the plain step.
+// is ~10^5 nodes) whose state stays in L2: a step is bound by launch and L2
+// latency rather than by HBM bandwidth, so it uses plain loads instead of
+// the staged pipeline of the plain step, and one launch with one shared
+// phi field instead of a phi pass through memory.
 #include <cuda_runtime.h>
 
 #include "lb_internal.h"
@@ -99,108 +108,139 @@ struct GeoView {
     __device__ __forceinline__ bool solid(int x, int y) const { return cls_at(x, y) != 0; }
 };
 
-template <typename Real>
-__device__ __forceinline__ Real phi_field(const Real* phi, const GeoView& G, int x, int y)
-{
-    return phi[(long long)wrap_near(y, G.ny) * G.nx + wrap_near(x, G.nx)];
-}
+// Tile of the fused obstacle step and its halos.
+constexpr int kGTX = 32, kGTY = 8;  // nodes of one CTA (one per thread)
+constexpr int kGH = 3;              // phi halo
+constexpr int kGC = kGH + 1;        // class-map halo
+constexpr int kGCX = kGTX + 2 * kGC, kGCY = kGTY + 2 * kGC;
+constexpr int kGPX = kGTX + 2 * kGH, kGPY = kGTY + 2 * kGH;
 
-// Wetting ghost value of the solid node (x, y) next to fluid.
-template <typename Real>
-__device__ Real ghost_phi(const DomDesc& D, const GeoView& G, const Real* phi, int x, int y)
+// periodic index for any offset (halos may exceed a small lattice)
+__device__ __forceinline__ int wrap_any(int v, int n)
 {
-    const int k = G.cls_at(x, y);
-    const Real h = k == -1 ? (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
-                 : k == -2 ? (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top))
-                           : class_h<Real>(D, k);
-    Real sum = Real(0);
-    int n = 0;
-    // axis directions (1,0), (-1,0), (0,1), (0,-1)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int dx = j == 0 ? 1 : (j == 1 ? -1 : 0);
-        const int dy = j == 2 ? 1 : (j == 3 ? -1 : 0);
-        if (!G.solid(x + dx, y + dy)) {
-            sum += phi_field(phi, G, x + D.wet_k * dx, y + D.wet_k * dy);
-            ++n;
-        }
-    }
-    if (n == 0) {
-        // diagonal directions (1,1), (-1,-1), (-1,1), (1,-1)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int dx = (j == 0 || j == 3) ? 1 : -1;
-            const int dy = (j == 0 || j == 2) ? 1 : -1;
-            if (!G.solid(x + dx, y + dy)) {
-                sum += phi_field(phi, G, x + D.wet_k * dx, y + D.wet_k * dy);
-                ++n;
-            }
-        }
-    }
-    const Real mean = n == 1 ? sum : (n == 2 ? sum * Real(0.5) : (n == 3 ? div_const<3>(sum) : sum * Real(0.25)));
-    return mean - Real(D.wet_k) * h;
-}
-
-// The nine pulled values of fluid node (x, y) from population set `src`
-// (nine planes of D.plane elements, logical column x at x + kXOff).
-template <typename Real>
-__device__ __forceinline__ void pull9(const DomDesc& D, const GeoView& G, const Real* src, int x,
-                                      int y, Real (&v)[9])
-{
-    const long long P = D.plane;
-    const long long own = (long long)y * D.pitch + x + kXOff;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int sx = x - gex(i), sy = y - gey(i);
-        if (i != 0 && G.solid(sx, sy)) {
-            v[i] = src[gopp(i) * P + own];
-        } else {
-            const long long o = (long long)wrap_near(sy, D.ny) * D.pitch + wrap_near(sx, D.nx) + kXOff;
-            v[i] = src[i * P + o];
-        }
-    }
-}
-
-template <typename Real>
-__global__ void __launch_bounds__(kGeoBlock) geo_phi_kernel(DomDesc D, int parity)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= D.nx) return;
-    const GeoView G{D.cls, D.nx, D.ny, D.walls};
-    if (D.cls[(long long)y * D.nx + x] != 0) return;
-    const Real* gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
-    Real g[9];
-    pull9<Real>(D, G, gs, x, y, g);
-    static_cast<Real*>(D.phi)[(long long)y * D.nx + x] = phi_sum<Real>(g);
+    const int r = v % n;
+    return r < 0 ? r + n : r;
 }
 
 template <typename Real, bool MRT>
-__global__ void __launch_bounds__(kGeoBlock) geo_step_kernel(DomDesc D, int parity)
+__global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int parity)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= D.nx) return;
-    const GeoView G{D.cls, D.nx, D.ny, D.walls};
-    if (D.cls[(long long)y * D.nx + x] != 0) return;
+    __shared__ signed char cl[kGCY][kGCX];
+    __shared__ Real ph[kGPY][kGPX];
+    __shared__ int colx[kGCX];  // wrapped column (+ kXOff) of each halo column
+    __shared__ int rowo[kGCY];  // offset of each halo row (wrapped row x pitch)
+    __shared__ int rowc[kGCY];  // the same row in the class map (wrapped row x nx)
+    const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
+    const int nx = D.nx, ny = D.ny;
     const Real* fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
     const Real* gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
-    Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
-    Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
-    const Real* phi = static_cast<const Real*>(D.phi);
+    // 0. periodic wrap of the halo coordinates, once per CTA
+    for (int k = threadIdx.x; k < kGCX + kGCY; k += blockDim.x) {
+        if (k < kGCX)
+            colx[k] = wrap_any(x0 - kGC + k, nx) + kXOff;
+        else {
+            const int wy = wrap_any(y0 - kGC + (k - kGCX), ny);
+            rowo[k - kGCX] = wy * D.pitch;
+            rowc[k - kGCX] = wy * nx;
+        }
+    }
+    __syncthreads();
+    // 1. class map (0 fluid, k > 0 solid class k, -1 / -2 bottom / top wall row)
+    for (int k = threadIdx.x; k < kGCX * kGCY; k += blockDim.x) {
+        const int cy = k / kGCX, cx = k - cy * kGCX;
+        const int y = y0 - kGC + cy;
+        int c;
+        if (D.walls && y < 0)
+            c = -1;
+        else if (D.walls && y >= ny)
+            c = -2;
+        else
+            c = D.cls[rowc[cy] + (colx[cx] - kXOff)];
+        cl[cy][cx] = static_cast<signed char>(c);
+    }
+    __syncthreads();
+    // lattice coordinates (unwrapped, within the halos) to shared memory
+    auto cls_l = [&](int x, int y) -> int { return cl[y - y0 + kGC][x - x0 + kGC]; };
+    auto phi_l = [&](int x, int y) -> Real { return ph[y - y0 + kGH][x - x0 + kGH]; };
+    auto off_l = [&](int x, int y) -> int { return rowo[y - y0 + kGC] + colx[x - x0 + kGC]; };
+    // the nine pulled values of fluid node (x, y) from population set src;
+    // a solid source bounces back (the node's own reversed population)
+    const long long P = D.plane;
+    auto pull = [&](const Real* src, int x, int y, Real (&v)[9]) {
+        const int own = off_l(x, y);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = x - gex(i), sy = y - gey(i);
+            if (i != 0 && cls_l(sx, sy) != 0)
+                v[i] = src[gopp(i) * P + own];
+            else
+                v[i] = src[i * P + off_l(sx, sy)];
+        }
+    };
+    // 2. phi of the tile and its halo (solid nodes: unused)
+    for (int k = threadIdx.x; k < kGPX * kGPY; k += blockDim.x) {
+        const int py = k / kGPX, px = k - py * kGPX;
+        const int x = x0 - kGH + px, y = y0 - kGH + py;
+        Real v = Real(0);
+        if (cls_l(x, y) == 0) {
+            Real g[9];
+            pull(gs, x, y, g);
+            v = phi_sum<Real>(g);
+        }
+        ph[py][px] = v;
+    }
+    __syncthreads();
+    // 3. the tile's fluid nodes
+    const int x = x0 + int(threadIdx.x) % kGTX, y = y0 + int(threadIdx.x) / kGTX;
+    if (x >= nx || y >= ny || cls_l(x, y) != 0) return;
     Real f[9], g[9];
-    pull9<Real>(D, G, fs, x, y, f);
-    pull9<Real>(D, G, gs, x, y, g);
+    pull(fs, x, y, f);
+    pull(gs, x, y, g);
     const Real c = phi_sum<Real>(g);
+    // wetting ghost value of solid node (sx, sy): the mean over the axis (or,
+    // through a corner only, the diagonal) directions d towards fluid of
+    // phi(s + k d) - k h, k = D.wet_k
+    auto ghost = [&](int sx, int sy) -> Real {
+        const int k = cls_l(sx, sy);
+        const Real h = k == -1 ? (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
+                     : k == -2 ? (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top))
+                               : class_h<Real>(D, k);
+        Real sum = Real(0);
+        int n = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int dx = j == 0 ? 1 : (j == 1 ? -1 : 0);
+            const int dy = j == 2 ? 1 : (j == 3 ? -1 : 0);
+            if (cls_l(sx + dx, sy + dy) == 0) {
+                sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
+                ++n;
+            }
+        }
+        if (n == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int dx = (j == 0 || j == 3) ? 1 : -1;
+                const int dy = (j == 0 || j == 2) ? 1 : -1;
+                if (cls_l(sx + dx, sy + dy) == 0) {
+                    sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
+                    ++n;
+                }
+            }
+        }
+        const Real mean = n == 1 ? sum : (n == 2 ? sum * Real(0.5) : (n == 3 ? div_const<3>(sum) : sum * Real(0.25)));
+        return mean - Real(D.wet_k) * h;
+    };
     // phi at the eight neighbours; ghost values at solid ones
     Real nb[9];
     bool next_to_solid = false;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int qx = x + gex(i), qy = y + gey(i);
-        if (G.solid(qx, qy)) {
+        if (cls_l(qx, qy) != 0) {
             next_to_solid = true;
-            nb[i] = ghost_phi<Real>(D, G, phi, qx, qy);
+            nb[i] = ghost(qx, qy);
         } else {
-            nb[i] = phi_field(phi, G, qx, qy);
+            nb[i] = phi_l(qx, qy);
         }
     }
     Real dx, dy, lap;
@@ -210,8 +250,9 @@ __global__ void __launch_bounds__(kGeoBlock) geo_step_kernel(DomDesc D, int pari
     Real fo[9], go[9];
     collide<Real, MRT>(prm, f, g, c, dx, dy, lap, D.step2 != 0 && next_to_solid,
                        D.step2_relax_j != 0, fo, go);
-    const long long P = D.plane;
-    const long long o = (long long)y * D.pitch + x + kXOff;
+    Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
+    Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
+    const int o = off_l(x, y);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         fd[i * P + o] = fo[i];
@@ -305,10 +346,8 @@ dim3 geo_grid(const DomDesc& d) { return dim3((d.nx + kGeoBlock - 1) / kGeoBlock
 template <typename Real, bool MRT>
 cudaError_t geo_step_t(const DomDesc& d, int parity, cudaStream_t s)
 {
-    geo_phi_kernel<Real><<<geo_grid(d), kGeoBlock, 0, s>>>(d, parity);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    geo_step_kernel<Real, MRT><<<geo_grid(d), kGeoBlock, 0, s>>>(d, parity);
+    const dim3 grid((d.nx + kGTX - 1) / kGTX, (d.ny + kGTY - 1) / kGTY);
+    geo_step_kernel<Real, MRT><<<grid, kGTX * kGTY, 0, s>>>(d, parity);
     return cudaGetLastError();
 }
 

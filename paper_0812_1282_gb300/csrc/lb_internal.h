@@ -50,10 +50,8 @@ struct DomDesc {
     float flut_lo, flut_step, flut_inv, flut_kmax;
     // Obstacles (nullptr: none).  cls[y * nx + x] = 0 for a fluid node, k in
     // 1..kMaxClass for a solid node of wetting class k with inward-normal
-    // wetting gradient hcls[k].  phi: per-node order parameter written by the
-    // first of the two kernels of an obstacle step ([ny][nx], Real).
+    // wetting gradient hcls[k].
     const unsigned char* cls;
-    void* phi;
     double hcls[8];
     float fhcls[8];
 };
@@ -97,7 +95,7 @@ int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, i
                      int cap, void* stream);
 int launch_fill_ghosts(int precision, const DomDesc& d, int parity, void* stream);
 
-// Domains with obstacles (d.cls != nullptr): one time step (two kernels),
+// Domains with obstacles (d.cls != nullptr): one time step (one kernel),
 // the initial equilibrium, and the rest state of the solid nodes of buffer b.
 int launch_geo_step(int precision, int coll, const DomDesc& d, int parity, void* stream);
 int launch_geo_init_eq(int precision, const DomDesc& d, const double* phi0, int parity,

@@ -147,7 +147,7 @@ def test_fp32_channel_within_1e5_after_1000_steps(lbf, orc):
 @pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
 def test_obstacle_free_map_equals_plain_kernel(lbf, orc, prec, tol, rule):
-    """The obstacle kernels on an all-fluid map and the staged plain kernel
+    """The obstacle kernel on an all-fluid map and the staged plain kernel
     compute the same arithmetic (the compiler may contract products into
     fused multiply-adds differently in the two kernels, so agreement is to
     rounding, not bitwise)."""
@@ -221,3 +221,32 @@ def test_geometry_errors(lbf):
     with pytest.raises(m.LBError):
         periodic.init_channel(10, 8, 0.0)
     periodic.close()
+
+
+@pytest.mark.parametrize("walls,nx,ny,block", [(True, 13, 9, (3, 6, 4, 7)),
+                                               (False, 11, 10, (2, 5, 3, 6)),
+                                               (True, 37, 11, (4, 7, 30, 34))])
+def test_small_obstacle_domains_match_oracle(lbf, orc, walls, nx, ny, block):
+    """Obstacle domains narrower or shorter than the step's tile and its
+    halos (a CTA covers 32 x 8 nodes plus three rings of phi), where the
+    halos wrap around the lattice several times: FP64 within 1e-12 of the
+    oracle."""
+    kw = dict(_kw(orc, "mrt"), walls=walls)
+    cls = np.zeros((ny, nx), np.uint8)
+    y0, y1, x0, x1 = block
+    cls[y0:y1, x0:x1] = 1
+    hc = [0.0, orc.wetting_h(70.0)]
+    phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 8)
+    ref = orc.OracleLattice(orc.params(**kw), nx, ny)
+    ref.set_geometry(cls, hc)
+    ref.init_phi(phi0)
+    sim = lbf.Lattice(lbf.params(precision="fp64", **kw), nx, ny)
+    sim.set_geometry(cls, hc)
+    sim.init_phi(phi0)
+    sim.step(211)
+    ref.step(211)
+    f, g = sim.populations()
+    fl = cls == 0
+    assert max_diff(f[:, fl], ref.f[:, fl]) <= 1e-12
+    assert max_diff(g[:, fl], ref.g[:, fl]) <= 1e-12
+    sim.close()
