@@ -216,8 +216,10 @@ class OracleLattice:
         self.hcls = None
 
     def set_geometry(self, cls: np.ndarray, hcls) -> None:
-        """cls: (ny, nx) uint8, 0 fluid, k in 1..7 solid of wetting class k;
-        hcls: the wetting gradient of each class (index 0 unused)."""
+        """cls: (ny, nx) uint8, 0 fluid, k in 1..7 solid of wetting class k,
+        8 a node-bounce-back wall node (rows 0 and ny - 1 of a walled
+        lattice only; its wetting gradient is h_bottom / h_top); hcls: the
+        wetting gradient of each solid class (index 0 unused)."""
         cls = np.ascontiguousarray(cls, dtype=np.uint8)
         assert cls.shape == (self.ny, self.nx)
         h = np.zeros(8)

@@ -602,13 +602,37 @@ int orc_step_window(const orc_params* p, int nx, int ny, int band_y0,
  *    diagonal directions are used the same way.  Every mirror node s + 2d
  *    must be fluid (features at least two nodes thick); otherwise the
  *    geometry is rejected.
- * On an obstacle-free lattice this is exactly the ghost-row rule above. */
+ * On an obstacle-free lattice this is exactly the ghost-row rule above.
+ *
+ * Node bounce-back (Fig. 4b: the wall lies on the boundary nodes; the paper
+ * gives no more), class ORC_NODE_WALL in row 0 or row ny - 1 of a walled
+ * lattice.  Read as the full-way scheme:
+ *  - a wall node streams like a fluid node (its pulls from beyond the
+ *    lattice take its own opposite population, as at a mid-link wall) and,
+ *    instead of colliding, reverses every population: f'_i = f_opp(i), the
+ *    same for g;
+ *  - for the stencils of its fluid neighbours its phi is the one-sided
+ *    wetting value across one spacing from the first fluid row,
+ *    phi(x, 0) = phi(x, 1) - h_bottom (phi(x, ny-1) = phi(x, ny-2) - h_top);
+ *  - fluid nodes next to a wall node are Step-2 boundary nodes;
+ *  - it carries no fluid of its own (its moments are not reported), but
+ *    its populations are part of the conserved totals;
+ *  - initially it holds the rest equilibrium of its wetting phi value. */
+#define ORC_NODE_WALL 8
+
+static int geo_node_wall(int nx, int ny, const unsigned char* cls, int x, int y)
+{
+    if (y < 0 || y >= ny) return 0;
+    return cls[(size_t)y * nx + wrap(x, nx)] == ORC_NODE_WALL;
+}
+
 static int geo_solid(const orc_params* p, int nx, int ny, const unsigned char* cls, int x, int y)
 {
     if (p->walls && (y < 0 || y >= ny)) return 1;
     x = wrap(x, nx);
     y = wrap(y, ny);
-    return cls[(size_t)y * nx + x] != 0;
+    const unsigned char c = cls[(size_t)y * nx + x];
+    return c != 0 && c != ORC_NODE_WALL;
 }
 
 static double geo_h(const orc_params* p, int nx, int ny, const unsigned char* cls,
@@ -650,12 +674,24 @@ int orc_geo_check(const orc_params* p, int nx, int ny, const unsigned char* cls)
     for (int y = -1; y <= ny; ++y) {
         if (!p->walls && (y < 0 || y >= ny)) continue;
         for (int x = 0; x < nx; ++x) {
+            if (y >= 0 && y < ny && cls[(size_t)y * nx + x] == ORC_NODE_WALL) {
+                /* node walls: outermost rows of a walled lattice of >= 4 rows,
+                 * with fluid in the rows next to them */
+                if (!p->walls || (y != 0 && y != ny - 1) || ny < 4) return -2;
+                if (cls[(size_t)(y == 0 ? 1 : ny - 2) * nx + x] != 0) return -1;
+                continue;
+            }
             if (y >= 0 && y < ny && cls[(size_t)y * nx + x] > 7) return -2;
             if (!geo_solid(p, nx, ny, cls, x, y)) continue;
             int dirs[4][2];
             const int n = geo_mirror_dirs(p, nx, ny, cls, x, y, dirs);
-            for (int k = 0; k < n; ++k)
-                if (geo_solid(p, nx, ny, cls, x + 2 * dirs[k][0], y + 2 * dirs[k][1])) return -1;
+            for (int k = 0; k < n; ++k) {
+                const int mx = x + 2 * dirs[k][0], my = y + 2 * dirs[k][1];
+                if (geo_solid(p, nx, ny, cls, mx, my)) return -1;
+                /* an obstacle's mirror node must be fluid, not a node wall
+                 * (the rows beyond a node wall are never mirrored) */
+                if (y >= 0 && y < ny && geo_node_wall(nx, ny, cls, mx, my)) return -1;
+            }
         }
     }
     return 0;
@@ -666,6 +702,10 @@ int orc_geo_check(const orc_params* p, int nx, int ny, const unsigned char* cls)
 static double geo_phi_at(const orc_params* p, int nx, int ny, const unsigned char* cls,
                          const double* hcls, const double* phi, int x, int y)
 {
+    if (geo_node_wall(nx, ny, cls, x, y)) {
+        const int in = y == 0 ? 1 : ny - 2; /* the first fluid row */
+        return phi[(size_t)in * nx + wrap(x, nx)] - (y == 0 ? p->h_bottom : p->h_top);
+    }
     if (!geo_solid(p, nx, ny, cls, x, y))
         return phi[(size_t)wrap(y, ny) * nx + wrap(x, nx)];
     int dirs[4][2];
@@ -721,7 +761,11 @@ int orc_init_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
     orc_phi_derivatives_geo(p, nx, ny, cls, hcls, phi0, dx, dy, lap);
     for (size_t k = 0; k < n; ++k) {
         double feq[9], geq[9];
-        if (cls[k] != 0) {
+        if (cls[k] == ORC_NODE_WALL) {
+            const int y = (int)(k / nx), x = (int)(k % nx);
+            const double pw = geo_phi_at(p, nx, ny, cls, hcls, phi0, x, y);
+            orc_node_equilibrium(p, 1.0, pw, 0.0, 0.0, 0.0, 0.0, 0.0, feq, geq);
+        } else if (cls[k] != 0) {
             for (int i = 0; i < 9; ++i) {
                 feq[i] = T[i];
                 geq[i] = 0.0;
@@ -761,13 +805,14 @@ int orc_step_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
     mrt_inverse(minv);
 
     for (int s = 0; s < nsteps; ++s) {
-        /* pull-stream with bounce-back from solid sources (fluid nodes only) */
+        /* pull-stream with bounce-back from solid sources (fluid and node-wall
+         * nodes) */
         int y;
 #pragma omp parallel for num_threads(orc_get_threads()) schedule(static)
         for (y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 const size_t k = (size_t)y * nx + x;
-                if (cls[k] != 0) continue;
+                if (cls[k] != 0 && cls[k] != ORC_NODE_WALL) continue;
                 for (int i = 0; i < 9; ++i) {
                     const int sx = x - EX[i], sy = y - EY[i];
                     size_t src;
@@ -811,10 +856,20 @@ int orc_step_geo(const orc_params* p, int nx, int ny, const unsigned char* cls,
         for (y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 const size_t kk = (size_t)y * nx + x;
+                if (cls[kk] == ORC_NODE_WALL) {
+                    /* node bounce-back: every population reversed */
+                    for (int i = 0; i < 9; ++i) {
+                        f[(size_t)i * n + kk] = fs[(size_t)OPP[i] * n + kk];
+                        g[(size_t)i * n + kk] = gs[(size_t)OPP[i] * n + kk];
+                    }
+                    continue;
+                }
                 if (cls[kk] != 0) continue;
                 int next_to_solid = 0;
                 for (int i = 1; i < 9; ++i)
-                    if (geo_solid(p, nx, ny, cls, x + EX[i], y + EY[i])) next_to_solid = 1;
+                    if (geo_solid(p, nx, ny, cls, x + EX[i], y + EY[i]) ||
+                        geo_node_wall(nx, ny, cls, x + EX[i], y + EY[i]))
+                        next_to_solid = 1;
                 const int step2_node = p->zero_u_at_walls && next_to_solid;
                 double ueqx = ux[kk], ueqy = uy[kk];
                 if (step2_node) {
