@@ -382,6 +382,16 @@ def run_capillary(lbf, torch, steps=None):
     dt_steps = time_steps(sim, 2000, torch)
     st = sim.stats()
     sim.close()
+    # latency floor of the same kernel: one CTA's tile (32 x 8 nodes with a
+    # small block), stepped the same way; the capillary step cannot be faster
+    tiny = lbf.Lattice(p, 32, 8)
+    cls = np.zeros((8, 32), np.uint8)
+    cls[2:5, 10:14] = 1
+    tiny.set_geometry(cls, [0.0, 0.0])
+    tiny.init_phi(np.zeros((8, 32)))
+    tiny.step(64)
+    dt_floor = time_steps(tiny, 2000, torch)
+    tiny.close()
     t = np.array(ts, float)
     l = np.array(ls)
     nua = (c["params"]["tau_alpha"] - 0.5) / 3
@@ -395,12 +405,16 @@ def run_capillary(lbf, torch, steps=None):
     k_theory = gamma * c["ch_w"] * math.cos(math.radians(theta_a)) / 6.0
     return dict(steps=steps, fluid_nodes=fluid, job_seconds=wall,
                 step_us=dt_steps / 2000 * 1e6, mlups_fluid=fluid * 2000 / dt_steps / 1e6,
+                bound="latency", latency_floor_us=dt_floor / 2000 * 1e6,
+                floor_over_step=dt_floor / dt_steps,
                 l_final=float(l[-1]), theta_a_late=theta_a,
                 washburn_slope=slope, washburn_slope_theory=k_theory,
                 nonfinite=int(st["nonfinite"]),
-                note="obstacle path, one fused launch per step; front by lb_meniscus every 500 "
-                     "steps; Washburn fit (nu_a - nu_b) l^2/2 + nu_b L l vs t over the second "
-                     "half, theory gamma w cos(theta_a) / 6")
+                note="obstacle path, one fused launch per step (the state stays in L2, so "
+                     "launch and L2 latency bound it: latency_floor_us is the same kernel on a "
+                     "single 32 x 8 tile); front by lb_meniscus every 500 steps; Washburn fit "
+                     "(nu_a - nu_b) l^2/2 + nu_b L l vs t over the second half, theory "
+                     "gamma w cos(theta_a) / 6")
 
 
 BATCH_JOB_STEPS = 10000

@@ -184,8 +184,8 @@ int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
  * paper states bounce-back and the wetting condition for flat walls only,
  * and they are read here node by node).
  *  cls:     host array [ny][nx]; 0 marks a fluid node, k in 1..7 a solid node
- *           of wetting class k.  NULL removes the obstacles.  Copied before
- *           the call returns.
+ *           of wetting class k, 8 a node-bounce-back wall node (below).
+ *           NULL removes the obstacles.  Copied before the call returns.
  *  h_class: n_class (1..8) inward-normal wetting gradients, h_class[k] for
  *           class k (entry 0 unused).
  * Rules: a pull from a solid node is bounced back (mid-link, as at a wall);
@@ -197,10 +197,21 @@ int lb_contact_angle(lb_handle* h, int dom, double exclude, double* theta_deg,
  * the rest state and report rho = phi = u = 0; they are left out of the
  * statistics and of the interface points.  A domain with obstacles is
  * stepped by one plain kernel per step instead of the staged one.
+ * Node bounce-back (Fig. 4b, the wall lying on the boundary nodes; the
+ * paper gives no more detail): class 8 in row 0 or row ny - 1 of a walled
+ * domain of at least 4 rows, read as the full-way scheme.  A wall node
+ * streams like a fluid node (its pulls from beyond the domain bounce back)
+ * and reverses every population instead of colliding; its fluid neighbours
+ * see phi(x, 0) = phi(x, 1) - h_bottom (phi(x, ny - 1) = phi(x, ny - 2) -
+ * h_top) and are Step-2 nodes; it reports no moments of its own and is
+ * initialised to the rest equilibrium of that phi value.  The no-slip planes
+ * then lie half a spacing inside the wall-node rows.
  * The state must be initialised again afterwards (lb_init_*).
  * Errors: LB_ERR_INVALID_ARG for a class out of range or without a
- * gradient, a non-finite gradient, a map without fluid, or a solid node
- * whose mirror node s + 2d is solid (features thinner than two nodes). */
+ * gradient, a non-finite gradient, a map without fluid, a solid node whose
+ * mirror node s + 2d is solid or a wall node (features thinner than two
+ * nodes), or a wall node outside the outer rows of a walled domain of at
+ * least 4 rows or without fluid next to it. */
 int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const double* h_class,
                     int n_class);
 

@@ -643,6 +643,12 @@ static double geo_h(const orc_params* p, int nx, int ny, const unsigned char* cl
     return hcls[cls[(size_t)wrap(y, ny) * nx + wrap(x, nx)]];
 }
 
+/* Is (x, y) a fluid node (neither solid nor a wall node)? */
+static int geo_fluid(const orc_params* p, int nx, int ny, const unsigned char* cls, int x, int y)
+{
+    return !geo_solid(p, nx, ny, cls, x, y) && !geo_node_wall(nx, ny, cls, x, y);
+}
+
 /* Mirror directions of solid node (x, y): axis directions with a fluid
  * neighbour, else diagonal ones.  Returns how many (0: no fluid neighbour). */
 static int geo_mirror_dirs(const orc_params* p, int nx, int ny, const unsigned char* cls,
@@ -652,14 +658,14 @@ static int geo_mirror_dirs(const orc_params* p, int nx, int ny, const unsigned c
     static const int DG[4][2] = {{1, 1}, {-1, -1}, {-1, 1}, {1, -1}};
     int n = 0;
     for (int k = 0; k < 4; ++k)
-        if (!geo_solid(p, nx, ny, cls, x + AX[k][0], y + AX[k][1])) {
+        if (geo_fluid(p, nx, ny, cls, x + AX[k][0], y + AX[k][1])) {
             dirs[n][0] = AX[k][0];
             dirs[n][1] = AX[k][1];
             ++n;
         }
     if (n > 0) return n;
     for (int k = 0; k < 4; ++k)
-        if (!geo_solid(p, nx, ny, cls, x + DG[k][0], y + DG[k][1])) {
+        if (geo_fluid(p, nx, ny, cls, x + DG[k][0], y + DG[k][1])) {
             dirs[n][0] = DG[k][0];
             dirs[n][1] = DG[k][1];
             ++n;

@@ -740,19 +740,34 @@ bool fit_circle(const std::vector<double>& pts, double& xc, double& yc, double& 
 }
 
 // Host check of an obstacle map (the rules of the obstacle step): classes
-// in range, some fluid, and every solid node next to fluid (wall rows
-// included) has fluid mirror nodes s + 2d in the directions its ghost value
-// uses.
+// in range, some fluid, node-bounce-back wall nodes only in the outer rows of
+// a walled domain of at least four rows with fluid next to them, and every
+// solid node next to fluid (wall rows included) has fluid mirror nodes
+// s + 2d in the directions its ghost value uses.
 int check_geometry(const unsigned char* cls, int nx, int ny, int walls)
 {
-    auto solid = [&](int x, int y) {
-        if (walls && (y < 0 || y >= ny)) return true;
+    auto at = [&](int x, int y) {
         x = ((x % nx) + nx) % nx;
         y = ((y % ny) + ny) % ny;
-        return cls[size_t(y) * nx + x] != 0;
+        return int(cls[size_t(y) * nx + x]);
+    };
+    // for the mirror rule a wall node is not fluid (a mirror may not land on one)
+    auto solid = [&](int x, int y) {
+        if (walls && (y < 0 || y >= ny)) return true;
+        return at(x, y) != 0;
     };
     long long fluid = 0;
     for (size_t k = 0; k < size_t(nx) * ny; ++k) {
+        const int y = int(k / nx);
+        if (cls[k] == lbfe::kNodeWall) {
+            if (!walls || (y != 0 && y != ny - 1) || ny < 4)
+                return fail(LB_ERR_INVALID_ARG,
+                            "node %zu: wall nodes (class %d) only in the outer rows of a walled "
+                            "domain of at least 4 rows", k, lbfe::kNodeWall);
+            if (cls[k + (y == 0 ? nx : -nx)] != 0)
+                return fail(LB_ERR_INVALID_ARG, "node %zu: a wall node needs fluid next to it", k);
+            continue;
+        }
         if (cls[k] > lbfe::kMaxClass)
             return fail(LB_ERR_INVALID_ARG, "class %d at node %zu exceeds %d", int(cls[k]), k,
                         lbfe::kMaxClass);
@@ -764,6 +779,10 @@ int check_geometry(const unsigned char* cls, int nx, int ny, int walls)
     for (int y = walls ? -1 : 0; y < (walls ? ny + 1 : ny); ++y)
         for (int x = 0; x < nx; ++x) {
             if (!solid(x, y)) continue;
+            // wall nodes and the solid rows beyond them take no ghost value
+            if (y >= 0 && y < ny && at(x, y) == lbfe::kNodeWall) continue;
+            if (y < 0 && at(x, 0) == lbfe::kNodeWall) continue;
+            if (y >= ny && at(x, ny - 1) == lbfe::kNodeWall) continue;
             int n = 0;
             for (auto& d : AX)
                 if (!solid(x + d[0], y + d[1])) {
@@ -1042,7 +1061,7 @@ int lb_set_geometry(lb_handle* h, int dom, const unsigned char* cls, const doubl
             if (!std::isfinite(h_class[k]))
                 return fail(LB_ERR_INVALID_ARG, "wetting gradient of class %d is not finite", k);
         for (size_t q = 0; q < size_t(D.nx) * D.ny; ++q)
-            if (cls[q] >= n_class)
+            if (cls[q] >= n_class && cls[q] != lbfe::kNodeWall)
                 return fail(LB_ERR_INVALID_ARG, "node %zu has class %d but only %d classes given",
                             q, int(cls[q]), n_class);
         rc = check_geometry(cls, D.nx, D.ny, D.walls);

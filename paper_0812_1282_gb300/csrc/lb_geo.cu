@@ -16,6 +16,13 @@
 //     plain step, so both paths agree there.
 // With walls, the rows y = -1 and y = ny are solid with h_bot / h_top.
 //
+// Node bounce-back (the paper's Fig. 4b, the wall on the boundary nodes),
+// class kNodeWall in row 0 or ny - 1 of a walled domain, read as the
+// full-way scheme: a wall node streams like a fluid node (its pulls from
+// beyond the domain bounce back) and reverses every population instead of
+// colliding; its fluid neighbours see phi(x, 0) = phi(x, 1) - h_bot (phi(x,
+// ny-1) = phi(x, ny-2) - h_top) and are Step-2 nodes.
+//
 // A step is one launch.  A CTA owns a tile of kGTX x kGTY nodes (one per
 // thread) and, in shared memory:
 //   1. the class map of the tile and a kGC-node halo;
@@ -161,6 +168,11 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
     __syncthreads();
     // lattice coordinates (unwrapped, within the halos) to shared memory
     auto cls_l = [&](int x, int y) -> int { return cl[y - y0 + kGC][x - x0 + kGC]; };
+    // a population pulled from a solid node bounces back (wall nodes stream)
+    auto solid_l = [&](int x, int y) {
+        const int c = cls_l(x, y);
+        return c != 0 && c != kNodeWall;
+    };
     auto phi_l = [&](int x, int y) -> Real { return ph[y - y0 + kGH][x - x0 + kGH]; };
     auto off_l = [&](int x, int y) -> int { return rowo[y - y0 + kGC] + colx[x - x0 + kGC]; };
     // the nine pulled values of fluid node (x, y) from population set src;
@@ -171,7 +183,7 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sx = x - gex(i), sy = y - gey(i);
-            if (i != 0 && cls_l(sx, sy) != 0)
+            if (i != 0 && solid_l(sx, sy))
                 v[i] = src[gopp(i) * P + own];
             else
                 v[i] = src[i * P + off_l(sx, sy)];
@@ -190,12 +202,26 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
         ph[py][px] = v;
     }
     __syncthreads();
-    // 3. the tile's fluid nodes
+    // 3. the tile's fluid and wall nodes
     const int x = x0 + int(threadIdx.x) % kGTX, y = y0 + int(threadIdx.x) / kGTX;
-    if (x >= nx || y >= ny || cls_l(x, y) != 0) return;
+    if (x >= nx || y >= ny) return;
+    const int cme = cls_l(x, y);
+    if (cme != 0 && cme != kNodeWall) return;
+    Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
+    Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
+    const int o = off_l(x, y);
     Real f[9], g[9];
     pull(fs, x, y, f);
     pull(gs, x, y, g);
+    if (cme == kNodeWall) {
+        // node bounce-back: every population reversed, no collision
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fd[i * P + o] = f[gopp(i)];
+            gd[i * P + o] = g[gopp(i)];
+        }
+        return;
+    }
     const Real c = phi_sum<Real>(g);
     // wetting ghost value of solid node (sx, sy): the mean over the axis (or,
     // through a corner only, the diagonal) directions d towards fluid of
@@ -236,7 +262,13 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int qx = x + gex(i), qy = y + gey(i);
-        if (cls_l(qx, qy) != 0) {
+        const int cq = cls_l(qx, qy);
+        if (cq == kNodeWall) {
+            // one-sided wetting value from the first fluid row
+            next_to_solid = true;
+            nb[i] = qy == 0 ? phi_l(qx, 1) - (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
+                            : phi_l(qx, ny - 2) - (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top));
+        } else if (cq != 0) {
             next_to_solid = true;
             nb[i] = ghost(qx, qy);
         } else {
@@ -250,9 +282,6 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
     Real fo[9], go[9];
     collide<Real, MRT>(prm, f, g, c, dx, dy, lap, D.step2 != 0 && next_to_solid,
                        D.step2_relax_j != 0, fo, go);
-    Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
-    Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
-    const int o = off_l(x, y);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         fd[i * P + o] = fo[i];
@@ -274,7 +303,17 @@ __global__ void geo_init_eq_kernel(DomDesc D, const double* __restrict__ phi0, i
     const long long o = (long long)y * D.pitch + x + kXOff;
     const GeoView G{D.cls, D.nx, D.ny, D.walls};
     double fe[9], ge[9];
-    if (D.cls[(long long)y * D.nx + x] != 0) {
+    const int cme = D.cls[(long long)y * D.nx + x];
+    if (cme == kNodeWall) {
+        // the rest equilibrium of the wall node's wetting phi value
+        const int in = y == 0 ? 1 : D.ny - 2;
+        const double pw = phi0[(long long)in * D.pitch + x] - (y == 0 ? D.h_bot : D.h_top);
+        NodeParams<double> prm{D.a, D.kappa, D.gamma, D.omega_phi, D.tau_c0, D.tau_c1, D.h_bot, D.h_top};
+        double m7, m8;
+        equilibria<double>(prm, 0.0, pw, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, fe, ge, m7, m8);
+        fe[0] = -((((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
+        ge[0] = pw - ((((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8]))));
+    } else if (cme != 0) {
         for (int i = 0; i < 9; ++i) fe[i] = ge[i] = 0.0;
     } else {
         // phi0 is laid out with pitch D.pitch; wrap it into a compact view
@@ -309,7 +348,10 @@ __global__ void geo_init_eq_kernel(DomDesc D, const double* __restrict__ phi0, i
         double nb[9];
         for (int i = 1; i < 9; ++i) {
             const int qx = x + gex(i), qy = y + gey(i);
-            nb[i] = G.solid(qx, qy) ? ghost(qx, qy) : at(qx, qy);
+            if (qy >= 0 && qy < D.ny && G.cls_at(qx, qy) == kNodeWall)
+                nb[i] = qy == 0 ? at(qx, 1) - D.h_bot : at(qx, D.ny - 2) - D.h_top;
+            else
+                nb[i] = G.solid(qx, qy) ? ghost(qx, qy) : at(qx, qy);
         }
         const double c = at(x, y);
         double dx, dy, lap, m7, m8;

@@ -57,6 +57,9 @@ struct DomDesc {
 };
 
 constexpr int kMaxClass = 7;
+// Class of a node-bounce-back wall node (rows 0 and ny - 1 of a walled
+// domain; the wetting gradient is the wall's h_bot / h_top).
+constexpr int kNodeWall = 8;
 
 // A rectangular piece of one domain processed by one CTA: columns
 // [x0, x0 + cols) and rows [y0, y0 + rows).  cols = 0 means the kernel's
