@@ -811,7 +811,9 @@ def experiment_ramp():
 def experiment_stripe():
     """The spurious-current stripe of Sec. IV.A: 28 x 15, a stripe of alpha
     across the channel between neutral walls, 20000 steps; BGK and MRT at
-    tau 10 / 10 (the paper's case) and at the viscosity ratios 12.5 and 10.
+    tau 10 / 10 (the paper's case) and at the viscosity ratios 12.5 and 10,
+    with mid-link walls and with node bounce-back walls (Fig. 4b: the same
+    15 fluid rows between rows of wall nodes).
     Reports max |u| and the bulge of the stripe's edge (its x at mid-height
     less its x on the wall row; negative: barrel shaped), FP64 and FP32 on
     the GPU; prints one JSON object."""
@@ -834,21 +836,36 @@ def experiment_stripe():
         return float("nan")
 
     rows = []
-    for coll in ("bgk", "mrt"):
-        for ta, tb in c["taus"]:
-            for prec in ("fp64", "fp32"):
-                p = lbf.params(collision=coll, tau_alpha=ta, tau_beta=tb, precision=prec, **cp)
-                sim = lbf.Lattice(p, c["nx"], c["ny"])
-                sim.init_phi(phi0)
-                sim.step(c["steps"])
-                _, phi, ux, uy, st = sim.moments()
-                sim.close()
-                bulge = left_edge(phi[c["ny"] // 2]) - left_edge(phi[0])
-                rows.append([coll, ta, tb, prec, float("%.4e" % np.hypot(ux, uy).max()),
-                             round(bulge, 4), int(st["nonfinite"])])
+    for walls in ("mid-link", "node"):
+        for coll in ("bgk", "mrt"):
+            for ta, tb in c["taus"]:
+                for prec in ("fp64", "fp32"):
+                    p = lbf.params(collision=coll, tau_alpha=ta, tau_beta=tb, precision=prec,
+                                   **cp)
+                    if walls == "node":
+                        # the same 15 fluid rows between rows of wall nodes (Fig. 4b)
+                        ny = c["ny"] + 2
+                        sim = lbf.Lattice(p, c["nx"], ny)
+                        cls = np.zeros((ny, c["nx"]), np.uint8)
+                        cls[0] = cls[-1] = 8
+                        sim.set_geometry(cls, [0.0])
+                        sim.init_phi(np.tile(prof, (ny, 1)))
+                        first = 1
+                    else:
+                        ny = c["ny"]
+                        sim = lbf.Lattice(p, c["nx"], ny)
+                        sim.init_phi(phi0)
+                        first = 0
+                    sim.step(c["steps"])
+                    _, phi, ux, uy, st = sim.moments()
+                    sim.close()
+                    bulge = left_edge(phi[ny // 2]) - left_edge(phi[first])
+                    rows.append([walls, coll, ta, tb, prec,
+                                 float("%.4e" % np.hypot(ux, uy).max()), round(bulge, 4),
+                                 int(st["nonfinite"])])
     print(json.dumps({"experiment": "stripe", "steps": c["steps"],
-                      "columns": ["collision", "tau_alpha", "tau_beta", "precision", "max_u",
-                                  "bulge", "nonfinite"], "rows": rows}), flush=True)
+                      "columns": ["walls", "collision", "tau_alpha", "tau_beta", "precision",
+                                  "max_u", "bulge", "nonfinite"], "rows": rows}), flush=True)
 
 
 def main():
