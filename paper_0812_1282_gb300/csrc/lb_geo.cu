@@ -189,8 +189,17 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
                 v[i] = src[i * P + off_l(sx, sy)];
         }
     };
-    // 2. phi of the tile and its halo (solid nodes: unused)
-    for (int k = threadIdx.x; k < kGPX * kGPY; k += blockDim.x) {
+    const int xq = x0 + int(threadIdx.x) % kGTX, yq = y0 + int(threadIdx.x) / kGTX;
+    const bool live = xq < nx && yq < ny && (cls_l(xq, yq) == 0 || cls_l(xq, yq) == kNodeWall);
+    Real fpre[9];
+    if (live) pull(fs, xq, yq, fpre);
+    // 2. phi of the tile and its halo (solid nodes: unused); a fixed trip
+    // count lets the loads of all of a thread's positions be in flight at once
+    constexpr int kPhiIters = (kGPX * kGPY + kGTX * kGTY - 1) / (kGTX * kGTY);
+#pragma unroll
+    for (int it = 0; it < kPhiIters; ++it) {
+        const int k = int(threadIdx.x) + it * kGTX * kGTY;
+        if (k >= kGPX * kGPY) break;
         const int py = k / kGPX, px = k - py * kGPX;
         const int x = x0 - kGH + px, y = y0 - kGH + py;
         Real v = Real(0);
@@ -211,7 +220,8 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
     Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
     const int o = off_l(x, y);
     Real f[9], g[9];
-    pull(fs, x, y, f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fpre[i];
     pull(gs, x, y, g);
     if (cme == kNodeWall) {
         // node bounce-back: every population reversed, no collision
