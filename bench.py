@@ -430,7 +430,19 @@ def batch_params(lbf, specs, compact):
                        step2_relax_momentum=True, compact_g=compact) for s in specs]
 
 
-def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_steps=None):
+# The five-class ladder the autotuner picks for the 256 drops (strips of 184,
+# 308, 370, 432 and 556 columns, 64 rows): a fixed schedule for profiling runs.
+LADDER_BX = (96, 160, 192, 224, 288)
+
+
+def ladder_schedule(lbf, rows=64):
+    strip = lambda bx: (62 * (bx // 32) - 2) // 4 * 4
+    return lbf.schedule(list(LADDER_BX), rows, ctas_per_sm=0,
+                        max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1)
+
+
+def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_steps=None,
+                fixed_schedule=False):
     """The 256 sessile drops (sides 64..512) of the batched workload: the
     whole 10000-step job in one batched handle per GPU (the autotuner picks
     the schedule), timed from the first step to the last; then, on a single
@@ -455,7 +467,11 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
             batch.init_drop(specs[d]["R"], specs[d]["cx"], specs[d]["cy"], dom=k)
 
     init()
-    tile = batch.autotune(reps=2)
+    if fixed_schedule:
+        batch.set_schedule(ladder_schedule(lbf))
+        tile = batch.tile()
+    else:
+        tile = batch.autotune(reps=2)
     sched = batch.schedule()
     batch.step(128)  # builds the step graphs
     init()
@@ -620,7 +636,8 @@ def ours(args):
         # one extra workload alone (profiling aid): its JSON object only
         if args.only == "batched":
             res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact",
-                              ws=ws, rank=rank, job_steps=args.job_steps)
+                              ws=ws, rank=rank, job_steps=args.job_steps,
+                              fixed_schedule=args.schedule == "ladder")
             if rank != 0:
                 return
         elif args.only == "fp64":
@@ -885,6 +902,9 @@ def main():
                     help="run one extra workload alone for --steps steps (profiling aid)")
     ap.add_argument("--job-steps", type=int, default=None,
                     help="steps of the batched job (profiling aid; default 10000)")
+    ap.add_argument("--schedule", choices=("auto", "ladder"), default="auto",
+                    help="batched job: autotuned schedule, or the fixed five-class ladder "
+                         "(profiling aid: no autotuning launches before the job)")
     ap.add_argument("--experiment", choices=("ramp", "stripe"), default=None,
                     help="run a physics experiment instead of the benchmark and print its "
                          "JSON table (ramp: the quasi-static wetting ramp of Sec. IV; stripe: "
