@@ -37,7 +37,7 @@ def _rank_main(rank, ws, port, elapsed, out):
 def test_max_over_ranks_and_job_value_gloo():
     ws, port = 2, _free_port()
     elapsed = [0.5, 2.0]
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(ws, port, elapsed, out), nprocs=ws, join=True)
         res = dict(out)

@@ -97,7 +97,7 @@ def test_split_run_gathers_the_single_process_table_gloo():
     specs = lbinputs.batch_specs(**SPECS)
     single = [_run_domain(oracle, s) for s in specs]
     ws, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
