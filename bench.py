@@ -435,10 +435,14 @@ def batch_params(lbf, specs, compact):
 LADDER_BX = (96, 160, 192, 224, 288)
 
 
-def ladder_schedule(lbf, rows=64):
+# fixed batched schedules (--schedule): (rows per item, persistent launches)
+FIXED_SCHEDULES = {"ladder": (64, 0), "ladder-persist": (32, 1)}
+
+
+def ladder_schedule(lbf, rows=64, persist=0):
     strip = lambda bx: (62 * (bx // 32) - 2) // 4 * 4
     return lbf.schedule(list(LADDER_BX), rows, ctas_per_sm=0,
-                        max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1)
+                        max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1, persist=persist)
 
 
 def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_steps=None,
@@ -468,7 +472,7 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
 
     init()
     if fixed_schedule:
-        batch.set_schedule(ladder_schedule(lbf))
+        batch.set_schedule(ladder_schedule(lbf, *fixed_schedule))
         tile = batch.tile()
     else:
         tile = batch.autotune(reps=2)
@@ -637,7 +641,7 @@ def ours(args):
         if args.only == "batched":
             res = run_batched(lbf, torch, max(4, args.steps), compact=args.storage == "compact",
                               ws=ws, rank=rank, job_steps=args.job_steps,
-                              fixed_schedule=args.schedule == "ladder")
+                              fixed_schedule=FIXED_SCHEDULES.get(args.schedule))
             if rank != 0:
                 return
         elif args.only == "fp64":
@@ -902,9 +906,10 @@ def main():
                     help="run one extra workload alone for --steps steps (profiling aid)")
     ap.add_argument("--job-steps", type=int, default=None,
                     help="steps of the batched job (profiling aid; default 10000)")
-    ap.add_argument("--schedule", choices=("auto", "ladder"), default="auto",
+    ap.add_argument("--schedule", choices=("auto", "ladder", "ladder-persist"), default="auto",
                     help="batched job: autotuned schedule, or the fixed five-class ladder "
-                         "(profiling aid: no autotuning launches before the job)")
+                         "(one launch per class per step, or per class per graph of "
+                         "persistent launches; profiling aid: no autotuning launches)")
     ap.add_argument("--experiment", choices=("ramp", "stripe"), default=None,
                     help="run a physics experiment instead of the benchmark and print its "
                          "JSON table (ramp: the quasi-static wetting ramp of Sec. IV; stripe: "

@@ -307,10 +307,33 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  *               (the classes hold disjoint domains, so they only meet at the
  *               graph's end); 0 launches the classes one after the other
  *               every step.
+ *  persist:     1 runs all the steps of an lb_step call (of each captured
+ *               graph of them) for a class in ONE launch of a persistent
+ *               kernel (compact FP32 storage only): its CTAs take (step,
+ *               work item) tickets in order from a device counter, and a
+ *               work item's step waits, by a bounded spin on device flags,
+ *               only for the items of its own domain that its halo reaches
+ *               to finish the step before, not for the whole GPU.  Then
+ *               ctas_per_sm[k] = 0 gives each class a share of the GPU in
+ *               proportion to its rows (the classes, launched side by side,
+ *               finish together); n >= 1 fixes n CTAs per SM.  A wait that
+ *               gives up makes lb_step report LB_ERR_TIMEOUT.
+ *  fill_pct:    persistent schedules: the shared-out CTAs of all classes
+ *               fill this percentage of the GPU's registers, shared memory
+ *               and thread slots (0 = 100; above 100 some CTAs wait for
+ *               room and start when a class finishes).
+ *  seal_edges:  compact storage: 1 makes a strip that covers its whole
+ *               domain also zero the padding and (stale) ghost columns that
+ *               share a 32-byte sector with its rows' first and last nodes,
+ *               so that no sector is written in part (the memory reads a
+ *               partly written sector before writing it back): a gain where
+ *               memory bandwidth binds, a few instructions more per row
+ *               elsewhere.
  * Results do not depend on the schedule (bit for bit).  A single-domain
  * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
- * Errors: LB_ERR_INVALID_ARG for a value out of range or max_nx not
- * increasing. */
+ * Errors: LB_ERR_INVALID_ARG for a value out of range, max_nx not
+ * increasing, persist without compact FP32 storage, fill_pct outside
+ * [0, 400], or seal_edges not 0 or 1. */
 #define LB_MAX_SCHED_CLASSES 8
 typedef struct lb_schedule {
     int n_class;
@@ -320,6 +343,9 @@ typedef struct lb_schedule {
     int ctas_per_sm[LB_MAX_SCHED_CLASSES];
     int order;
     int chains;
+    int persist;
+    int fill_pct;
+    int seal_edges;
 } lb_schedule;
 int lb_set_schedule(lb_handle* h, const lb_schedule* s);
 int lb_get_schedule(const lb_handle* h, lb_schedule* s);
@@ -349,12 +375,14 @@ long long lb_launch_count(const lb_handle* h);
 const char* lb_error_string(int code);
 const char* lb_last_error(void);
 
-/* Self-check of the device-side wait bound used by the step kernel (the
+/* Self-check of the device-side wait bounds used by the step kernels (the
  * paper has no counterpart): one warp waits on a barrier that nothing ever
- * completes; the wait must give up after its wall-time bound (200 ms) and
- * report it.  Returns LB_ERR_TIMEOUT when the bound works (the expected
- * result), LB_OK if the wait was satisfied (a defect), LB_ERR_CUDA on a
- * launch error.  Synchronises `stream`; leaves the context usable. */
+ * completes (the stage waits), another on a step flag that nothing ever
+ * sets (the persistent batched kernel's wait for its neighbours); each wait
+ * must give up after its wall-time bound (200 ms) and report it.  Returns
+ * LB_ERR_TIMEOUT when both bounds work (the expected result), LB_OK if a
+ * wait did not give up (a defect), LB_ERR_CUDA on a launch error.
+ * Synchronises `stream`; leaves the context usable. */
 int lb_check_wait_timeout(void* stream);
 
 /* Measured FP64 throughput of the current device (the paper has no

@@ -83,7 +83,8 @@ class Schedule(ctypes.Structure):
         ("block_x", ctypes.c_int * LB_MAX_SCHED_CLASSES),
         ("rows", ctypes.c_int * LB_MAX_SCHED_CLASSES),
         ("ctas_per_sm", ctypes.c_int * LB_MAX_SCHED_CLASSES),
-        ("order", ctypes.c_int), ("chains", ctypes.c_int),
+        ("order", ctypes.c_int), ("chains", ctypes.c_int), ("persist", ctypes.c_int),
+        ("fill_pct", ctypes.c_int), ("seal_edges", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -91,13 +92,17 @@ class Schedule(ctypes.Structure):
         return {"n_class": n, "max_nx": list(self.max_nx)[:max(n - 1, 0)],
                 "block_x": list(self.block_x)[:n], "rows": list(self.rows)[:n],
                 "ctas_per_sm": list(self.ctas_per_sm)[:n], "order": self.order,
-                "chains": self.chains}
+                "chains": self.chains, "persist": self.persist, "fill_pct": self.fill_pct,
+                "seal_edges": self.seal_edges}
 
 
-def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1) -> Schedule:
+def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1, persist=0,
+             fill_pct=0, seal_edges=0) -> Schedule:
     """Schedule block; block_x, rows and ctas_per_sm are per class (an int
     applies to every class); max_nx gives the class limits (n_class - 1
-    values)."""
+    values); persist=1 runs each class's steps in one persistent launch
+    (fill_pct: the share of the GPU its CTAs fill); seal_edges=1 makes
+    whole-domain strips write whole sectors."""
     n = len(max_nx) + 1
 
     def per_class(v):
@@ -108,7 +113,8 @@ def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1) -> Sche
     arr = ctypes.c_int * LB_MAX_SCHED_CLASSES
     return Schedule(n, arr(*(list(max_nx) + [0] * (LB_MAX_SCHED_CLASSES - len(max_nx)))),
                     arr(*per_class(block_x)), arr(*per_class(rows)), arr(*per_class(ctas_per_sm)),
-                    int(order), int(chains))
+                    int(order), int(chains), int(persist), int(fill_pct),
+                    int(seal_edges))
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,

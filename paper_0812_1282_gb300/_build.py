@@ -20,7 +20,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbfe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lb_kernels.cu", "lb_api.cu", "lb_noalloc.cu", "lb_geo.cu", "lb_step_f32.cu",
-           "lb_step_f64.cu", "lb_peak.cu"]
+           "lb_step_persist.cu", "lb_step_f64.cu", "lb_peak.cu"]
 
 
 def nvcc() -> str:

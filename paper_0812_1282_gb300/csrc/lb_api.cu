@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -46,6 +47,11 @@ constexpr int kMinBlockX = 32;
 constexpr int kMaxBlockX = 256;
 constexpr int kMaxBlockXCompact = 288;
 constexpr int kGraphBig = 64;
+// Items a work item of a persistent schedule may wait for: its own and the
+// two neighbouring row blocks on each side (a short last block can bring
+// the second one within reach), each in its own and the two neighbouring
+// strips.
+constexpr int kMaxDeps = 15;
 constexpr int kGraphSmall = 2;
 constexpr int kChunk = 1 << 20;  // nodes per staging chunk for host field output
 
@@ -68,6 +74,7 @@ struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
     std::vector<size_t> geo_off;    // domain d's obstacle map (nx*ny bytes)
+    size_t flags = 0, dep_off = 0, dep_idx = 0;  // persistent schedules (batches)
     size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0,
            sched = 0;
     size_t total = 0;
@@ -110,6 +117,12 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
     off = align_up(off + sizeof(DomDesc) * n_dom, kAlign);
     L.items = off;
     off = align_up(off + sizeof(WorkItem) * (n_dom > 1 ? item_cap : 1), kAlign);
+    L.flags = off;
+    off = align_up(off + sizeof(int) * (n_dom > 1 ? item_cap : 1), kAlign);
+    L.dep_off = off;
+    off = align_up(off + sizeof(int) * (n_dom > 1 ? item_cap + 1 : 1), kAlign);
+    L.dep_idx = off;
+    off = align_up(off + sizeof(int) * (n_dom > 1 ? item_cap * kMaxDeps : 1), kAlign);
     L.partials = off;
     off = align_up(off + sizeof(double) * lbfe::kStatsFields * lbfe::max_partials_needed(0, 0),
                    kAlign);
@@ -179,6 +192,7 @@ struct lb_handle {
     cudaStream_t cap_stream = nullptr;
     int device = 0;
     int sm_count = 0;
+    int regs_per_sm = 65536, smem_per_sm = 0, threads_per_sm = 2048;
     // Launch shape of a single domain (class 0's) and the batch schedule;
     // cls_begin / cls_count: each class's slice of the device work list.
     lb_schedule sched{};
@@ -188,6 +202,8 @@ struct lb_handle {
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[LB_MAX_SCHED_CLASSES - 1] = {nullptr};
     int n_items = 0;
+    // persistent schedules: CTAs of each class's launch
+    int pgrid[LB_MAX_SCHED_CLASSES] = {0};
     // compact g storage: a strip that covers its whole domain takes the
     // periodic wrap from its own stage copy and leaves the ghost columns
     // alone, so after steps they may be stale; they are refreshed before
@@ -202,6 +218,9 @@ struct lb_handle {
 
     DomDesc* d_descs() const { return reinterpret_cast<DomDesc*>(base + L.descs); }
     WorkItem* d_items() const { return reinterpret_cast<WorkItem*>(base + L.items); }
+    int* d_flags() const { return reinterpret_cast<int*>(base + L.flags); }
+    int* d_dep_off() const { return reinterpret_cast<int*>(base + L.dep_off); }
+    int* d_dep_idx() const { return reinterpret_cast<int*>(base + L.dep_idx); }
     double* d_partials() const { return reinterpret_cast<double*>(base + L.partials); }
     StatsOut* d_stats() const { return reinterpret_cast<StatsOut*>(base + L.stats); }
     double* d_pts() const { return reinterpret_cast<double*>(base + L.pts); }
@@ -231,6 +250,140 @@ int class_of(const lb_handle* h, int nx)
     return h->sched.n_class - 1;
 }
 
+// Dependencies of the work items of a persistent schedule (compact storage).
+// Item i's step reads compact rows y0 - 2 .. y1 + 1 and f rows y0 - 1 .. y1
+// of its strip and 4 columns on each side (periodic in x, and in y without
+// walls), and writes rows y0 .. y1 - 1 of its strip (and, at a domain edge,
+// the ghost columns the strip across the wrap reads).  It waits for every
+// item of its domain whose written rows meet its read rows in its own or a
+// neighbouring strip: the same items have then also finished reading what
+// item i overwrites.  CSR over the whole list: dep_off[i] .. dep_off[i + 1]
+// index dep_idx, whose entries are class-local item indices.
+int build_deps(lb_handle* h, const std::vector<WorkItem>& items, std::vector<int>& dep_off,
+               std::vector<int>& dep_idx)
+{
+    dep_off.assign(items.size() + 1, 0);
+    dep_idx.clear();
+    for (int c = 0; c < h->sched.n_class; ++c) {
+        const int b0 = h->cls_begin[c], n = h->cls_count[c];
+        if (n == 0) continue;
+        // (domain, row block, strip) -> class-local index
+        std::unordered_map<long long, int> at;
+        auto key = [](int d, int b, int k) {
+            return ((long long)d << 40) | ((long long)b << 20) | (long long)k;
+        };
+        std::vector<int> nstrip(h->n_dom, 0), width(h->n_dom, 1);
+        for (int li = 0; li < n; ++li) {
+            const WorkItem& w = items[b0 + li];
+            if (w.x0 == 0) width[w.dom] = w.cols > 0 ? w.cols : h->sched.block_x[c];
+        }
+        for (int li = 0; li < n; ++li) {
+            const WorkItem& w = items[b0 + li];
+            const int k = w.x0 / width[w.dom];
+            nstrip[w.dom] = std::max(nstrip[w.dom], k + 1);
+            at[key(w.dom, w.y0 / h->sched.rows[c], k)] = li;
+        }
+        for (int li = 0; li < n; ++li) {
+            const WorkItem& w = items[b0 + li];
+            const DomDesc& D = h->descs[w.dom];
+            const int rows = h->sched.rows[c];
+            const int nb = (D.ny + rows - 1) / rows, K = nstrip[w.dom];
+            const int b = w.y0 / rows, k = w.x0 / width[w.dom];
+            const int lo = w.y0 - 2, hi = w.y0 + w.rows + 2;  // read rows [lo, hi)
+            std::vector<int> mine;
+            for (int db = -2; db <= 2; ++db) {
+                int bb = b + db;
+                if (D.walls && (bb < 0 || bb >= nb)) continue;
+                bb = ((bb % nb) + nb) % nb;
+                const int y0 = bb * rows, y1 = std::min(y0 + rows, D.ny);
+                bool meet = false;
+                for (int sh = D.walls ? 0 : -1; sh <= (D.walls ? 0 : 1) && !meet; ++sh)
+                    meet = y0 + sh * D.ny < hi && y1 + sh * D.ny > lo;
+                if (!meet) continue;
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int kk = ((k + dk) % K + K) % K;
+                    auto f = at.find(key(w.dom, bb, kk));
+                    if (f == at.end()) return fail(LB_ERR_INVALID_ARG, "work list is not a grid");
+                    if (std::find(mine.begin(), mine.end(), f->second) == mine.end())
+                        mine.push_back(f->second);
+                }
+            }
+            if (int(mine.size()) > kMaxDeps)
+                return fail(LB_ERR_INVALID_ARG, "persistent schedule: item has %d neighbours",
+                            int(mine.size()));
+            dep_off[b0 + li] = int(dep_idx.size());
+            dep_idx.insert(dep_idx.end(), mine.begin(), mine.end());
+        }
+    }
+    dep_off[items.size()] = int(dep_idx.size());
+    return LB_OK;
+}
+
+// CTAs of each class's persistent launch.  ctas_per_sm[c] > 0 fixes them
+// (per SM, at most one per item); 0 shares the GPU out so that the classes,
+// launched side by side, finish together: a CTA's pace is about one row per
+// pipeline iteration whatever its width, so class c gets CTAs in proportion
+// to its rows (plus the pipeline's five lead-in stages per item), scaled so
+// that the CTAs of all classes fill fill_pct percent of the GPU (a CTA takes
+// the larger of its shares of an SM's registers, shared memory and threads).
+void persist_grids(lb_handle* h, const std::vector<WorkItem>& items)
+{
+    double work[LB_MAX_SCHED_CLASSES] = {0}, cost[LB_MAX_SCHED_CLASSES] = {0};
+    bool fixed[LB_MAX_SCHED_CLASSES] = {false};
+    double room = (h->sched.fill_pct > 0 ? h->sched.fill_pct : 100) / 100.0;
+    for (int c = 0; c < h->sched.n_class; ++c) {
+        h->pgrid[c] = 0;
+        const int n = h->cls_count[c];
+        if (n == 0) continue;
+        const int bx = h->sched.block_x[c];
+        // a pipeline iteration of a wider CTA takes a little longer (more
+        // warps meet at its barrier): measured about 1 + (NW - 3) / 23
+        const double pace = (bx / 32 + 20) / 23.0;
+        for (int li = 0; li < n; ++li) work[c] += (items[h->cls_begin[c] + li].rows + 5) * pace;
+        int regs = 0;
+        size_t smem = 0;
+        double share = 1.0;
+        if (lbfe::persist_footprint(h->coll, bx, &regs, &smem) == 0 && h->smem_per_sm > 0) {
+            const double threads = bx + 32;
+            const double warp_regs = double((regs + 7) / 8 * 8) * 32.0;  // allocated per warp
+            share = std::max({warp_regs * threads / 32.0 / h->regs_per_sm,
+                              double(smem + 1024) / h->smem_per_sm, threads / h->threads_per_sm});
+        } else {
+            share = 1.0 / std::max(1, lbfe::persist_occupancy(h->coll, bx));
+        }
+        cost[c] = share / h->sm_count;
+        if (h->sched.ctas_per_sm[c] > 0) {
+            h->pgrid[c] = std::min(h->sched.ctas_per_sm[c] * h->sm_count, n);
+            fixed[c] = true;
+            room -= h->pgrid[c] * cost[c];
+        }
+    }
+    // proportional shares; a class capped at one CTA per item gives its
+    // spare room back to the others
+    for (int pass = 0; pass < LB_MAX_SCHED_CLASSES; ++pass) {
+        double demand = 0.0;
+        for (int c = 0; c < h->sched.n_class; ++c)
+            if (h->cls_count[c] > 0 && !fixed[c]) demand += work[c] * cost[c];
+        if (demand <= 0.0) break;
+        const double alpha = std::max(room, 0.0) / demand;
+        bool capped = false;
+        for (int c = 0; c < h->sched.n_class; ++c) {
+            if (h->cls_count[c] == 0 || fixed[c]) continue;
+            if (alpha * work[c] >= h->cls_count[c]) {
+                h->pgrid[c] = h->cls_count[c];
+                fixed[c] = true;
+                room -= h->pgrid[c] * cost[c];
+                capped = true;
+            }
+        }
+        if (capped) continue;
+        for (int c = 0; c < h->sched.n_class; ++c)
+            if (h->cls_count[c] > 0 && !fixed[c])
+                h->pgrid[c] = std::max(1, std::min(h->cls_count[c], int(alpha * work[c] + 0.5)));
+        break;
+    }
+}
+
 // Work list for the batched kernel: every (domain, x strip, row block),
 // grouped by schedule class (class c's items are one contiguous slice).
 int build_items(lb_handle* h)
@@ -255,15 +408,16 @@ int build_items(lb_handle* h)
                 const int wmax = lbfe::compact_strip(bx);
                 const int k = (D.nx + wmax - 1) / wmax;
                 const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
+                const int seal = h->sched.seal_edges ? lbfe::kItemSeal : 0;
                 for (int y0 = 0; y0 < D.ny; y0 += rows)
                     for (int x0 = 0; x0 < D.nx; x0 += w)
                         mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0),
-                                                std::min(w, D.nx - x0)});
+                                                std::min(w, D.nx - x0), seal});
                 continue;
             }
             for (int y0 = 0; y0 < D.ny; y0 += rows)
                 for (int x0 = 0; x0 < D.nx; x0 += bx)
-                    mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0), 0});
+                    mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0), 0, 0});
         }
         if (h->sched.order == 1) {
             // largest first: nodes of the item (the full-storage strip is
@@ -286,6 +440,16 @@ int build_items(lb_handle* h)
     if (!items.empty())
         LB_CUDA(cudaMemcpyAsync(h->d_items(), items.data(), sizeof(WorkItem) * items.size(),
                                 cudaMemcpyHostToDevice, h->stream));
+    std::vector<int> dep_off, dep_idx;
+    if (h->sched.persist && !items.empty()) {
+        const int rc = build_deps(h, items, dep_off, dep_idx);
+        if (rc != LB_OK) return rc;
+        LB_CUDA(cudaMemcpyAsync(h->d_dep_off(), dep_off.data(), sizeof(int) * dep_off.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+        LB_CUDA(cudaMemcpyAsync(h->d_dep_idx(), dep_idx.data(), sizeof(int) * dep_idx.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+        persist_grids(h, items);
+    }
     LB_CUDA(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
@@ -308,6 +472,35 @@ int launch_class(lb_handle* h, int c, int parity, cudaStream_t s)
         return fail(LB_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
     return LB_OK;
 }
+
+// The persistent launch of schedule class c: `len` steps, step k reading
+// buffer parity ^ (k & 1), or always `parity` with fixed_parity.
+int launch_persist_class(lb_handle* h, int c, int len, int parity, bool fixed_parity,
+                         cudaStream_t s)
+{
+    if ((long long)h->cls_count[c] * len >= (1LL << 31))
+        return fail(LB_ERR_INVALID_ARG, "persistent launch: too many (step, item) tickets");
+    lbfe::PersistLaunch a{};
+    a.descs = h->d_descs();
+    a.items = h->d_items() + h->cls_begin[c];
+    a.dep_off = h->d_dep_off() + h->cls_begin[c];
+    a.dep_idx = h->d_dep_idx();
+    a.flags = h->d_flags() + h->cls_begin[c];
+    a.sched = h->d_sched(c);
+    a.err = h->d_err();
+    a.n_items = h->cls_count[c];
+    a.n_steps = len;
+    a.parity0 = parity;
+    a.flip = fixed_parity ? 0 : 1;
+    a.bx = h->sched.block_x[c];
+    a.grid = h->pgrid[c];
+    const int e = lbfe::launch_persist(h->coll, a, s);
+    if (e != 0)
+        return fail(LB_ERR_CUDA, "persistent step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    return LB_OK;
+}
+
+bool persistent(const lb_handle* h) { return h->n_dom > 1 && h->sched.persist != 0; }
 
 // Kernel launches of one time step.
 long long launches_per_step(const lb_handle* h)
@@ -349,7 +542,8 @@ int enqueue_step(lb_handle* h, int parity, cudaStream_t s)
     } else {
         for (int c = 0; c < h->sched.n_class; ++c) {
             if (h->cls_count[c] == 0) continue;
-            const int rc = launch_class(h, c, parity, s);
+            const int rc = persistent(h) ? launch_persist_class(h, c, 1, parity, false, s)
+                                         : launch_class(h, c, parity, s);
             if (rc != LB_OK) return rc;
         }
     }
@@ -364,6 +558,14 @@ int active_classes(const lb_handle* h)
     return h->n_dom == 1 ? 0 : n;
 }
 
+// Kernel launches of `len` steps (a persistent schedule runs each class's
+// steps in one launch).
+long long launches_for(const lb_handle* h, int len)
+{
+    if (!persistent(h)) return len * launches_per_step(h);
+    return active_classes(h) + (long long)len * h->n_geo;
+}
+
 // Enqueue `len` steps on `s` (the capture stream).  With several schedule
 // classes and chains on, each class runs its `len` launches as its own
 // chain on its own stream, forked from `s` at the start and joined back at
@@ -373,6 +575,28 @@ int active_classes(const lb_handle* h)
 int enqueue_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStream_t s)
 {
     auto par = [&](int k) { return fixed_parity ? parity : parity ^ (k & 1); };
+    // a class's `len` steps: one persistent launch, or a launch per step
+    auto class_steps = [&](int c, cudaStream_t sc) -> int {
+        if (persistent(h)) return launch_persist_class(h, c, len, parity, fixed_parity, sc);
+        for (int k = 0; k < len; ++k) {
+            const int rc = launch_class(h, c, par(k), sc);
+            if (rc != LB_OK) return rc;
+        }
+        return LB_OK;
+    };
+    if (persistent(h) && !(h->sched.chains && active_classes(h) > 1)) {
+        for (int k = 0; k < h->sched.n_class; ++k) {
+            const int c = h->sched.n_class - 1 - k;
+            if (h->cls_count[c] == 0) continue;
+            const int rc = class_steps(c, s);
+            if (rc != LB_OK) return rc;
+        }
+        for (int k = 0; k < len; ++k) {
+            const int rc = enqueue_geo(h, par(k), s);
+            if (rc != LB_OK) return rc;
+        }
+        return LB_OK;
+    }
     if (!(h->sched.chains && active_classes(h) > 1)) {
         for (int k = 0; k < len; ++k) {
             const int rc = enqueue_step(h, par(k), s);
@@ -382,17 +606,18 @@ int enqueue_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStre
     }
     LB_CUDA(cudaEventRecord(h->fork_ev, s));
     int used = 0;
-    for (int c = 0; c < h->sched.n_class; ++c) {
+    // persistent launches widest class first: its CTAs, the largest, find
+    // room before the smaller ones fill the gaps
+    for (int k = 0; k < h->sched.n_class; ++k) {
+        const int c = persistent(h) ? h->sched.n_class - 1 - k : k;
         if (h->cls_count[c] == 0) continue;
         cudaStream_t sc = s;
         if (used > 0) {
             sc = h->chain[used - 1];
             LB_CUDA(cudaStreamWaitEvent(sc, h->fork_ev, 0));
         }
-        for (int k = 0; k < len; ++k) {
-            const int rc = launch_class(h, c, par(k), sc);
-            if (rc != LB_OK) return rc;
-        }
+        const int rc = class_steps(c, sc);
+        if (rc != LB_OK) return rc;
         if (used > 0) LB_CUDA(cudaEventRecord(h->join_ev[used - 1], sc));
         ++used;
     }
@@ -501,13 +726,20 @@ int finish_init(lb_handle* h, int dom)
     // current buffer, phi0 sat in the other one
     const DomDesc& D = h->descs[dom];
     int e;
+    // phi0 is consumed once the equilibria are written: clear its scratch, so
+    // that the idle buffer's padding columns, which no step reads and only
+    // sealing whole-domain strips overwrite (with zeros), hold zeros whatever
+    // the schedule, and checkpoints do not depend on it
+    const size_t scratch = sizeof(double) * size_t(D.plane);
     if (D.cls) {
         e = lbfe::launch_geo_init_eq(h->precision, D, phi0_scratch(h, dom), h->parity, h->stream);
-        // solid nodes of the idle buffer (phi0 is consumed by now): rest state
+        if (e == 0) e = int(cudaMemsetAsync(phi0_scratch(h, dom), 0, scratch, h->stream));
+        // solid nodes of the idle buffer: rest state
         if (e == 0) e = lbfe::launch_geo_solid_rest(h->precision, D, h->parity ^ 1, h->stream);
         h->launches += 2;
     } else {
         e = lbfe::launch_init_eq(h->precision, D, phi0_scratch(h, dom), h->parity, h->stream);
+        if (e == 0) e = int(cudaMemsetAsync(phi0_scratch(h, dom), 0, scratch, h->stream));
         h->launches += 1;
     }
     if (e != 0) return fail(LB_ERR_CUDA, "init launch failed: %s", cudaGetErrorString(cudaError_t(e)));
@@ -571,6 +803,12 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         return bail(fail(LB_ERR_CUDA, "kernel setup failed: %s", cudaGetErrorString(e)));
     if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
             cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor,
+                                    h->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                    h->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor,
+                                    h->device)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(fail(LB_ERR_CUDA, "device setup failed: %s", cudaGetErrorString(e)));
     if (n_dom > 1) {
@@ -929,7 +1167,7 @@ int lb_step(lb_handle* h, int n)
         }
         if (len & 1) h->parity ^= 1;
         h->steps += len;
-        h->launches += len * launches_per_step(h);
+        h->launches += launches_for(h, len);
         n -= len;
     }
     return LB_OK;
@@ -1439,8 +1677,15 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
             (sc->max_nx[c] < 1 || (c > 0 && sc->max_nx[c] <= sc->max_nx[c - 1])))
             return fail(LB_ERR_INVALID_ARG, "max_nx must be positive and increasing");
     }
-    if ((sc->order != 0 && sc->order != 1) || (sc->chains != 0 && sc->chains != 1))
-        return fail(LB_ERR_INVALID_ARG, "order and chains must be 0 or 1");
+    if ((sc->order != 0 && sc->order != 1) || (sc->chains != 0 && sc->chains != 1) ||
+        (sc->persist != 0 && sc->persist != 1))
+        return fail(LB_ERR_INVALID_ARG, "order, chains and persist must be 0 or 1");
+    if (sc->fill_pct < 0 || sc->fill_pct > 400)
+        return fail(LB_ERR_INVALID_ARG, "fill_pct must be in [0, 400]");
+    if (sc->seal_edges != 0 && sc->seal_edges != 1)
+        return fail(LB_ERR_INVALID_ARG, "seal_edges must be 0 or 1");
+    if (sc->persist && h->n_dom > 1 && !(h->precision == LB_FP32 && h->descs[0].compact))
+        return fail(LB_ERR_INVALID_ARG, "persistent schedules need compact FP32 storage");
     const int rg = refresh_ghosts(h);  // the new schedule may split a domain into strips
     if (rg != LB_OK) return rg;
     LB_CUDA(cudaStreamSynchronize(h->stream));
@@ -1487,7 +1732,7 @@ double time_graph_steps(lb_handle* h, int len, int reps, cudaEvent_t e0, cudaEve
         fail(LB_ERR_CUDA, "autotune launch failed");
     }
     cudaGraphExecDestroy(g);
-    h->launches += (long long)(reps + 1) * len * launches_per_step(h);
+    h->launches += (long long)(reps + 1) * launches_for(h, len);
     return ms_step;
 }
 
@@ -1531,19 +1776,31 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
         ladders = {{64, 128, 256}, {64, 128, 192, 256}};
     else
         ladders = {{64, 128}};
+    auto ladder = [&](const std::vector<int>& lad, int r, int persist, int seal) {
+        lb_schedule s{};
+        s.n_class = int(lad.size());
+        s.chains = 1;
+        s.order = 1;
+        s.persist = persist;
+        s.seal_edges = seal;
+        s.fill_pct = persist ? 85 : 0;
+        for (int c = 0; c < s.n_class; ++c) {
+            s.block_x[c] = lad[c];
+            s.rows[c] = r;
+            s.ctas_per_sm[c] = 0;
+            s.max_nx[c] = compact ? lbfe::compact_strip(lad[c]) : lad[c];
+        }
+        out.push_back(s);
+    };
     for (const auto& lad : ladders)
-        for (int r : {48, 64, 96, 128}) {
-            lb_schedule s{};
-            s.n_class = int(lad.size());
-            s.chains = 1;
-            s.order = 1;
-            for (int c = 0; c < s.n_class; ++c) {
-                s.block_x[c] = lad[c];
-                s.rows[c] = r;
-                s.ctas_per_sm[c] = 0;
-                s.max_nx[c] = compact ? lbfe::compact_strip(lad[c]) : lad[c];
-            }
-            out.push_back(s);
+        for (int r : {48, 64, 96, 128}) ladder(lad, r, 0, 0);
+    if (compact && h->precision == LB_FP32)
+        for (const auto& lad : ladders) {
+            // the same ladders with sealed rows, and as persistent launches
+            // (each class's steps in one launch, the GPU shared out between
+            // the classes)
+            for (int r : {32, 64}) ladder(lad, r, 0, 1);
+            for (int r : {32, 64}) ladder(lad, r, 1, 0);
         }
     return out;
 }
@@ -1605,12 +1862,14 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
             return -1.0;
         return double(t) / r;
     };
-    // a batch: a few steps per graph, so that chains and tails show as they
-    // will in the step graphs; then the fastest few again over longer graphs
-    // (the short timings of neighbouring candidates are within noise)
+    // a batch: a few steps per graph (16 for a persistent schedule, whose
+    // launch fills and drains the GPU once per graph), so that chains and
+    // tails show; then the fastest few again over graphs of the length the
+    // steps run in (the short timings of neighbouring candidates are within
+    // noise)
     std::vector<std::pair<double, size_t>> scored;
     for (size_t k = 0; k < cands.size(); ++k) {
-        const double ms = time_candidate(cands[k], 4, reps);
+        const double ms = time_candidate(cands[k], cands[k].persist ? 16 : 4, reps);
         if (ms < 0.0) {
             if (rc == LB_OK) rc = LB_ERR_CUDA;
             break;
@@ -1621,7 +1880,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
         std::sort(scored.begin(), scored.end());
         const size_t top = std::min<size_t>(6, scored.size());
         for (size_t t = 0; t < top && rc == LB_OK; ++t) {
-            const double ms = time_candidate(cands[scored[t].second], 16, reps + 2);
+            const double ms = time_candidate(cands[scored[t].second], kGraphBig, reps + 1);
             if (ms < 0.0) {
                 if (rc == LB_OK) rc = LB_ERR_CUDA;
                 break;
@@ -1662,8 +1921,8 @@ int lb_check_wait_timeout(void* stream)
     unsigned word = 0;
     const int e = lbfe::run_wait_selfcheck(stream, &word);
     if (e != 0) return fail(LB_ERR_CUDA, "self-check launch failed: %s", cudaGetErrorString(cudaError_t(e)));
-    if (word != 0) return fail(LB_ERR_TIMEOUT, "bounded wait gave up as designed (word 0x%x)", word);
-    return LB_OK;
+    if (word == 3u) return fail(LB_ERR_TIMEOUT, "bounded waits gave up as designed (word 0x%x)", word);
+    return fail(LB_OK, "a bounded wait did not give up (word 0x%x)", word);
 }
 
 const char* lb_error_string(int code)

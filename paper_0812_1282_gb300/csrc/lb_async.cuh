@@ -151,6 +151,51 @@ __device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, u
     }
 }
 
+// Step flags of the persistent batched kernel (ints in global memory,
+// shared by the CTAs of one launch): a release store publishes a count after
+// the writer's earlier stores, an acquire load orders the reader's later
+// accesses after it.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// order generic-proxy accesses of global memory with later bulk copies
+// (async proxy) of the same memory
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Wait until *flag >= need; bounded like mbar_wait (gives up after kWaitNs,
+// or at once when another waiter has recorded a failure).
+__device__ __forceinline__ bool flag_wait(const int* flag, int need, unsigned* err)
+{
+    if (ld_acquire_gpu(flag) >= need) return true;
+    unsigned long long t0 = 0;
+    for (unsigned n = 1;; ++n) {
+        __nanosleep(64);
+        if (ld_acquire_gpu(flag) >= need) return true;
+        if (n % kPollCheck == 0) {
+            const unsigned long long now = global_ns();
+            if (n == kPollCheck) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                if (err) atomicOr(err, kErrTimeout);
+                return false;
+            }
+            if (err && *reinterpret_cast<volatile unsigned*>(err)) return false;
+        }
+    }
+}
+
 // Named CTA barrier `id` (1..15) over the `nthreads` threads (a multiple of
 // 32, whole converged warps) that execute it; orders their shared-memory
 // accesses like __syncthreads.  A hardware barrier, not a poll: it is used

@@ -66,7 +66,9 @@ constexpr int kNodeWall = 8;
 // full strip width (clipped to the domain).
 struct WorkItem {
     int dom, x0, y0, rows, cols;
+    int flags;  // kItemSeal: a whole-domain strip completes its rows' edge sectors
 };
+constexpr int kItemSeal = 1;
 
 // Per-domain reduction result written by the moments kernels.
 struct StatsOut {
@@ -82,6 +84,27 @@ constexpr int kStatsFields = 6;
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x,
                 int rows, int grid_persistent, int* sched, void* stream);
+
+// One launch of the persistent multi-step batched compact kernel (FP32,
+// compact g storage) over one schedule class: items, dep_off (n_items + 1
+// entries) and flags are the class's slices; dep_idx holds class-local item
+// indices.
+struct PersistLaunch {
+    const DomDesc* descs;
+    const WorkItem* items;
+    const int* dep_off;
+    const int* dep_idx;
+    int* flags;
+    int* sched;
+    unsigned* err;
+    int n_items, n_steps, parity0, flip, bx, grid;
+};
+int launch_persist(int coll, const PersistLaunch& a, void* stream);
+// Resident CTAs per SM of the persistent kernel (0 on error), and its
+// shared-memory opt-in (once per device, outside any capture).
+int persist_occupancy(int coll, int block_x);
+int persist_footprint(int coll, int block_x, int* regs, size_t* smem);
+int prepare_persist();
 
 int launch_init_phi_drop(int precision, const DomDesc& d, double* phi0, double R, double cx,
                          double cy, void* stream);

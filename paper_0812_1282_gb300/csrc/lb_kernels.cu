@@ -25,6 +25,7 @@ int prepare_step_kernels()
 {
     int e = prepare_step_f32();
     if (e == 0) e = prepare_step_f64();
+    if (e == 0) e = prepare_persist();
     return e;
 }
 
@@ -543,9 +544,13 @@ int launch_crossings(int precision, const DomDesc& d, int parity, double* pts, i
 }
 
 // ------------------------------------------------ bounded-wait self-check
-// One warp waits on an mbarrier that nothing ever completes.  The wait must
-// give up after its wall-time bound and record the failure in the word.
-static __device__ unsigned g_selfcheck_err;
+// Warp 0 waits on an mbarrier that nothing ever completes (the stage waits
+// of the step kernels), warp 1 on a step flag that nothing ever sets (the
+// persistent batched kernel's wait for neighbouring work items).  Each wait
+// must give up after its wall-time bound and record the failure in its own
+// word.
+static __device__ unsigned g_selfcheck_err[2];
+static __device__ int g_selfcheck_flag;
 
 __global__ void wait_selfcheck_kernel()
 {
@@ -554,23 +559,33 @@ __global__ void wait_selfcheck_kernel()
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    __syncwarp();
-    mbar_wait(&bar, 0, &g_selfcheck_err);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        mbar_wait(&bar, 0, &g_selfcheck_err[0]);
+    else
+        flag_wait(&g_selfcheck_flag, 1, &g_selfcheck_err[1]);
 }
 
 int run_wait_selfcheck(void* stream, unsigned* word)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const unsigned zero = 0;
-    cudaError_t e = cudaMemcpyToSymbolAsync(g_selfcheck_err, &zero, sizeof(zero), 0,
+    const unsigned zero[2] = {0, 0};
+    const int zflag = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_selfcheck_err, zero, sizeof(zero), 0,
                                             cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbolAsync(g_selfcheck_flag, &zflag, sizeof(zflag), 0,
+                                    cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return int(e);
-    wait_selfcheck_kernel<<<1, 32, 0, s>>>();
+    wait_selfcheck_kernel<<<1, 64, 0, s>>>();
     if ((e = cudaGetLastError()) != cudaSuccess) return int(e);
-    e = cudaMemcpyFromSymbolAsync(word, g_selfcheck_err, sizeof(unsigned), 0,
-                                  cudaMemcpyDeviceToHost, s);
+    unsigned got[2] = {0, 0};
+    e = cudaMemcpyFromSymbolAsync(got, g_selfcheck_err, sizeof(got), 0, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return int(e);
-    return int(cudaStreamSynchronize(s));
+    e = cudaStreamSynchronize(s);
+    // bit 0: the barrier wait gave up, bit 1: the flag wait gave up
+    *word = (got[0] ? 1u : 0u) | (got[1] ? 2u : 0u);
+    return int(e);
 }
 
 }  // namespace lbfe

@@ -194,11 +194,13 @@ __device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<
 // parameters (and the wall wetting gradients) come from prm_shared, a copy
 // in shared memory read at each use, instead of registers held for the
 // whole tile (the batched form, whose parameters change from tile to tile).
+// seal: a whole-domain strip completes the edge sectors of its rows (below).
 template <bool MRT, int S, int NWC = 0, bool PRM_SMEM = false>
 __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int x0, int y0,
                                                int rows, int cols, unsigned char* __restrict__ smem,
                                                int nw, int cw, unsigned& q,
-                                               const NodeParams<float>* prm_shared = nullptr)
+                                               const NodeParams<float>* prm_shared = nullptr,
+                                               bool seal = false)
 {
     const int NW = NWC > 0 ? NWC : nw;
     float* __restrict__ fd = static_cast<float*>(parity ? D.f[0] : D.f[1]);
@@ -227,20 +229,21 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
     const int x = x0 + jn;
     // A strip that covers its whole domain takes the periodic wrap from its
     // own stage copy: lattice column c < 0 or c >= nx is read at stage
-    // index (c mod nx) + 4 instead of the ghost columns, which such a strip
-    // therefore neither reads nor writes.  Only the few lanes whose columns
+    // index (c mod nx) + 4 instead of the ghost columns, whose copies such a
+    // strip therefore neither uses nor keeps.  Only the few lanes whose columns
     // wrap do anything extra.  Expansion lane: columns je - 2, je - 1 of the
     // domain (stage indices ex0, ex1); collision lane: pulls across x = 0 or
     // x = nx - 1.
     // One bit mask keeps the lane's wrap cases (the indices are recomputed
     // on the rare path): 1 expansion columns wrap, 2 node jn pulls from
-    // x = -1, 4 node jn pulls from x = nx, 8 node jn + 1 pulls from x = nx.
+    // x = -1, 4 node jn pulls from x = nx, 8 node jn + 1 pulls from x = nx;
+    // 16 marks a whole strip, 32 one that seals its rows' edge sectors.
     const bool whole = x0 == 0 && ncols == nx;
     auto wrap_idx = [nx](int c) { return (c < 0 ? c + nx : (c >= nx ? c - nx : c)) + 4; };
     const unsigned wrapbits =
         whole ? (unsigned(wrap_idx(je - 2) != je + 2 || wrap_idx(je - 1) != je + 3) |
                  (unsigned(jn == 0) << 1) | (unsigned(jn + 1 == nx) << 2) |
-                 (unsigned(jn + 2 == nx) << 3))
+                 (unsigned(jn + 2 == nx) << 3) | 16u | (seal ? 32u : 0u))
               : 0u;
 
     auto slot_of = [&](int p) { return (qb + unsigned(p)) % unsigned(S); };
@@ -430,7 +433,7 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
             // in its stage copy instead)
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                if (whole) break;
+                if (wrapbits & 16u) break;
                 const int xl = x + l;
                 if (jn + l >= ncols) continue;
                 if (xl < 2) {
@@ -445,6 +448,24 @@ __device__ __forceinline__ void consume_tile_c(const DomDesc& D, int parity, int
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) cd[kk * P + o + l - nx] = co2[kk].lane(l);
                 }
+            }
+        }
+        // Sealing: a whole strip's node stores alone write the first and
+        // last 32-byte sector of each output row in part, and a partly
+        // written sector costs the memory a read before its write; so lanes
+        // 0..12 of warp 0 zero physical columns 0..3 of plane `lane` (slack
+        // and the ghost copies, stale in such a strip) and lanes 16..28 the
+        // columns past the last node up to the sector end.  It pays where
+        // the memory is the bound (many narrow domains in full use) and
+        // costs warp 0 some twenty instructions per row where latency is.
+        if ((wrapbits & 32u) && cw == 0 && p >= T.npro && (lane < 13 || (lane >= 16 && lane < 29))) {
+            const int pl = lane < 13 ? lane : lane - 16;
+            float* row = (pl < 9 ? fd + pl * P : cd + (pl - 9) * P) + (qr - 3) * pitch;
+            if (lane < 13) {
+                *reinterpret_cast<float4*>(row) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const int e = D.nx + kXOff;
+                for (int k = e; k < ((e + 7) & ~7); ++k) row[k] = 0.f;
             }
         }
         release(p);

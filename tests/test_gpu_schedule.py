@@ -67,14 +67,37 @@ def _schedules(lbf, compact):
         "three-classes": lbf.schedule([64, 96, 128], [32, 5, 64], ctas_per_sm=[1, 0, 2],
                                       max_nx=[100, 200], order=1),
         "empty-class": lbf.schedule([64, 128], 32, max_nx=[10]),
+        # persistent launches (compact storage): each class's steps in one
+        # launch, work items waiting on their neighbours' step flags
+        "multistep-ladder": lbf.schedule([96, 160, 288], 32, ctas_per_sm=0,
+                                         max_nx=[w(96), w(160)], order=1, persist=1),
+        # split strips and row blocks of 3 and 5 rows: an item waits on two
+        # row blocks on each side and on the strips beside it
+        "multistep-short-blocks": lbf.schedule([64, 128], [5, 3], ctas_per_sm=[0, 1],
+                                               max_nx=[w(64)], chains=0, persist=1),
+        # one CTA per SM: most items wait for a CTA to come free
+        "multistep-few-ctas": lbf.schedule(64, 16, ctas_per_sm=1, persist=1),
+        # over-filled: some CTAs start only when a class finishes
+        "multistep-overfilled-sealed": lbf.schedule([96, 160, 288], 32, ctas_per_sm=0,
+                                                    max_nx=[w(96), w(160)], order=1,
+                                                    persist=1, fill_pct=150, seal_edges=1),
+        # whole-domain strips that write whole sectors (zeroed ghost columns)
+        "sealed-ladder": lbf.schedule([96, 160, 288], 64, ctas_per_sm=0,
+                                      max_nx=[w(96), w(160)], order=1, seal_edges=1),
     }
+
+
+MULTISTEP = ("multistep-ladder", "multistep-short-blocks", "multistep-few-ctas",
+             "multistep-overfilled-sealed")
 
 
 @pytest.mark.parametrize("name", ["one-class-persistent", "one-item-per-cta-largest-first",
                                   "two-classes-chained", "two-classes-in-turn", "three-classes",
-                                  "empty-class"])
+                                  "empty-class", "sealed-ladder", *MULTISTEP])
 def test_schedule_gives_single_domain_results(lbf, single_states, name):
     compact, ref = single_states
+    if (name in MULTISTEP or name == "sealed-ladder") and not compact:
+        pytest.skip("persistent launches, sealing and 288-wide strips take compact storage")
     specs = _specs()
     plist = _plist(lbf, specs, compact)
     batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
@@ -122,7 +145,10 @@ def test_schedule_validation(lbf):
            lbf.schedule(128, 0),                                  # no rows
            lbf.schedule(128, 32, ctas_per_sm=33),                 # too many CTAs per SM
            lbf.schedule([64, 128, 128], 32, max_nx=[200, 100]),   # limits not increasing
-           lbf.schedule(128, 32, order=2)]
+           lbf.schedule(128, 32, order=2),
+           lbf.schedule(128, 32, persist=2),
+           lbf.schedule(128, 32, persist=1, fill_pct=401),
+           lbf.schedule(128, 32, seal_edges=2)]
     for sc in bad:
         with pytest.raises(lbf.LBError) as e:
             batch.set_schedule(sc)
@@ -132,19 +158,29 @@ def test_schedule_validation(lbf):
     with pytest.raises(lbf.LBError):
         batch.set_schedule(sc)
     batch.close()
+    # persistent launches are built for compact FP32 storage only
+    full = lbf.Batch(_plist(lbf, specs, False), [s["nx"] for s in specs],
+                     [s["ny"] for s in specs])
+    with pytest.raises(lbf.LBError) as e:
+        full.set_schedule(lbf.schedule(128, 32, persist=1))
+    assert e.value.code == lbf.LB_ERR_INVALID_ARG
+    full.close()
 
 
-@pytest.mark.parametrize("compact", [False, True], ids=["full-g", "compact-g"])
-def test_switching_schedules_midrun_matches_a_fixed_schedule(lbf, compact):
+@pytest.mark.parametrize("compact,persist", [(False, 0), (True, 0), (True, 1)],
+                         ids=["full-g", "compact-g", "compact-g-multistep"])
+def test_switching_schedules_midrun_matches_a_fixed_schedule(lbf, compact, persist):
     """Strips that cover a whole domain wrap in shared memory and leave the
     ghost columns alone (compact storage); a later schedule that splits the
     same domains into several strips must still see correct ghost columns.
     Whole -> split -> whole, with a checkpoint in between, against a run on
-    one split schedule throughout."""
+    one split schedule throughout (the whole-strip schedule also as
+    persistent multi-step launches)."""
     specs = _specs()
     plist = _plist(lbf, specs, compact)
     nxs, nys = [s["nx"] for s in specs], [s["ny"] for s in specs]
-    whole = lbf.schedule(256, 16, ctas_per_sm=0)       # every domain one strip
+    whole = lbf.schedule(256, 16, ctas_per_sm=0, persist=persist,  # every domain one strip
+                         seal_edges=persist)
     split = lbf.schedule(32, 7, ctas_per_sm=2, order=1)  # strips of 60 (compact) / 32 columns
 
     def init(b):
