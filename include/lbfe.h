@@ -322,18 +322,18 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  *               fill this percentage of the GPU's registers, shared memory
  *               and thread slots (0 = 100; above 100 some CTAs wait for
  *               room and start when a class finishes).
- *  seal_edges:  compact storage: 1 makes a strip that covers its whole
- *               domain also zero the padding and (stale) ghost columns that
- *               share a 32-byte sector with its rows' first and last nodes,
- *               so that no sector is written in part (the memory reads a
- *               partly written sector before writing it back): a gain where
- *               memory bandwidth binds, a few instructions more per row
- *               elsewhere.
+ *  seal_edges[k]: compact storage: 1 makes class k's strips that cover
+ *               their whole domain also zero the padding and (stale) ghost
+ *               columns that share a 32-byte sector with their rows' first
+ *               and last nodes, so that no sector is written in part (the
+ *               memory reads a partly written sector before writing it
+ *               back): a gain where memory bandwidth binds and rows are
+ *               short, a few instructions more per row elsewhere.
  * Results do not depend on the schedule (bit for bit).  A single-domain
  * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
  * Errors: LB_ERR_INVALID_ARG for a value out of range, max_nx not
  * increasing, persist without compact FP32 storage, fill_pct outside
- * [0, 400], or seal_edges not 0 or 1. */
+ * [0, 400], or a seal_edges value not 0 or 1. */
 #define LB_MAX_SCHED_CLASSES 8
 typedef struct lb_schedule {
     int n_class;
@@ -345,7 +345,7 @@ typedef struct lb_schedule {
     int chains;
     int persist;
     int fill_pct;
-    int seal_edges;
+    int seal_edges[LB_MAX_SCHED_CLASSES];
 } lb_schedule;
 int lb_set_schedule(lb_handle* h, const lb_schedule* s);
 int lb_get_schedule(const lb_handle* h, lb_schedule* s);

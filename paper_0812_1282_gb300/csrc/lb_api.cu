@@ -408,7 +408,7 @@ int build_items(lb_handle* h)
                 const int wmax = lbfe::compact_strip(bx);
                 const int k = (D.nx + wmax - 1) / wmax;
                 const int w = ((D.nx + k - 1) / k + 3) / 4 * 4;
-                const int seal = h->sched.seal_edges ? lbfe::kItemSeal : 0;
+                const int seal = h->sched.seal_edges[c] ? lbfe::kItemSeal : 0;
                 for (int y0 = 0; y0 < D.ny; y0 += rows)
                     for (int x0 = 0; x0 < D.nx; x0 += w)
                         mine.push_back(WorkItem{d, x0, y0, std::min(rows, D.ny - y0),
@@ -1673,6 +1673,8 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
                         c);
         if (sc->ctas_per_sm[c] < 0 || sc->ctas_per_sm[c] > 32)
             return fail(LB_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 32] (class %d)", c);
+        if (sc->seal_edges[c] != 0 && sc->seal_edges[c] != 1)
+            return fail(LB_ERR_INVALID_ARG, "seal_edges must be 0 or 1 (class %d)", c);
         if (c + 1 < sc->n_class &&
             (sc->max_nx[c] < 1 || (c > 0 && sc->max_nx[c] <= sc->max_nx[c - 1])))
             return fail(LB_ERR_INVALID_ARG, "max_nx must be positive and increasing");
@@ -1682,8 +1684,7 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
         return fail(LB_ERR_INVALID_ARG, "order, chains and persist must be 0 or 1");
     if (sc->fill_pct < 0 || sc->fill_pct > 400)
         return fail(LB_ERR_INVALID_ARG, "fill_pct must be in [0, 400]");
-    if (sc->seal_edges != 0 && sc->seal_edges != 1)
-        return fail(LB_ERR_INVALID_ARG, "seal_edges must be 0 or 1");
+
     if (sc->persist && h->n_dom > 1 && !(h->precision == LB_FP32 && h->descs[0].compact))
         return fail(LB_ERR_INVALID_ARG, "persistent schedules need compact FP32 storage");
     const int rg = refresh_ghosts(h);  // the new schedule may split a domain into strips
@@ -1696,6 +1697,7 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
         v.block_x[c] = v.block_x[0];
         v.rows[c] = v.rows[0];
         v.ctas_per_sm[c] = v.ctas_per_sm[0];
+        v.seal_edges[c] = v.seal_edges[0];
     }
     v.max_nx[v.n_class - 1] = 0;
     h->sched = v;
@@ -1776,19 +1778,20 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
         ladders = {{64, 128, 256}, {64, 128, 192, 256}};
     else
         ladders = {{64, 128}};
+    // seal: 0 none, 1 the narrowest class (the shortest rows), 2 every class
     auto ladder = [&](const std::vector<int>& lad, int r, int persist, int seal) {
         lb_schedule s{};
         s.n_class = int(lad.size());
         s.chains = 1;
         s.order = 1;
         s.persist = persist;
-        s.seal_edges = seal;
         s.fill_pct = persist ? 85 : 0;
         for (int c = 0; c < s.n_class; ++c) {
             s.block_x[c] = lad[c];
             s.rows[c] = r;
             s.ctas_per_sm[c] = 0;
             s.max_nx[c] = compact ? lbfe::compact_strip(lad[c]) : lad[c];
+            s.seal_edges[c] = seal == 2 || (seal == 1 && c == 0);
         }
         out.push_back(s);
     };
@@ -1799,7 +1802,8 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
             // the same ladders with sealed rows, and as persistent launches
             // (each class's steps in one launch, the GPU shared out between
             // the classes)
-            for (int r : {32, 64}) ladder(lad, r, 0, 1);
+            for (int r : {32, 64})
+                for (int seal : {1, 2}) ladder(lad, r, 0, seal);
             for (int r : {32, 64}) ladder(lad, r, 1, 0);
         }
     return out;

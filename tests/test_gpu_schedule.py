@@ -83,7 +83,7 @@ def _schedules(lbf, compact):
                                                     persist=1, fill_pct=150, seal_edges=1),
         # whole-domain strips that write whole sectors (zeroed ghost columns)
         "sealed-ladder": lbf.schedule([96, 160, 288], 64, ctas_per_sm=0,
-                                      max_nx=[w(96), w(160)], order=1, seal_edges=1),
+                                      max_nx=[w(96), w(160)], order=1, seal_edges=[1, 0, 1]),
     }
 
 
