@@ -442,7 +442,12 @@ FIXED_SCHEDULES = {"ladder": (64, 0), "ladder-persist": (32, 1)}
 def ladder_schedule(lbf, rows=64, persist=0):
     strip = lambda bx: (62 * (bx // 32) - 2) // 4 * 4
     return lbf.schedule(list(LADDER_BX), rows, ctas_per_sm=0,
-                        max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1, persist=persist)
+                        max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1, persist=persist,
+                        fill_pct=85 if persist else 0)
+
+
+# steps of the persistent-launch comparison on the batched workload
+PERSIST_CMP_STEPS = 640
 
 
 def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_steps=None,
@@ -493,6 +498,19 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
         except lbf.LBError:
             th = float("nan")
         rows[d] = [th, st["max_u"], float(st["nonfinite"])]
+    persist_cmp = None
+    if compact and ws == 1 and not fixed_schedule:
+        # the same ladder as persistent multi-step launches (each class's
+        # steps of a 64-step graph in one launch), for comparison
+        batch.set_schedule(ladder_schedule(lbf, 32, persist=1))
+        batch.step(128)
+        torch.cuda.synchronize()
+        dt_p = time_steps(batch, PERSIST_CMP_STEPS, torch)
+        n_all = sum(nodes_d)
+        persist_cmp = dict(steps_timed=PERSIST_CMP_STEPS,
+                           mlups=round(n_all * PERSIST_CMP_STEPS / dt_p / 1e6, 1),
+                           achieved_gbs=round(n_all * PERSIST_CMP_STEPS * 104 / dt_p / 1e9, 1),
+                           schedule=batch.schedule())
     batch.close()
     table = shard.gather_rows(len(specs), 3, rows, device="cuda" if ws > 1 else "cpu")
     nodes = sum(nodes_d)
@@ -506,6 +524,8 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
                schedule=sched, tile=list(tile[:2]),
                storage="compact g" if compact else "full",
                nonfinite_domains=sum(1 for r in table if r[2] > 0))
+    if persist_cmp is not None:
+        res["persistent_launches"] = persist_cmp
     if ws > 1:
         res.update(parallelism="%d ranks, node-balanced split of the domains (greedy, "
                                "largest first), no data-path collective" % ws,
@@ -567,7 +587,9 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
                     "relaxing Step-2 reading; angle_err_max_deg = the timed run's angles "
                     "against the FP64 oracle's (tests/golden/batch_angles.json, 16 smallest "
                     "domains, compact and full storage both tested in "
-                    "tests/test_gpu_batch_angles.py)" % (job, loop_steps))
+                    "tests/test_gpu_batch_angles.py); persistent_launches = the five-class "
+                    "ladder (32 rows) as persistent multi-step launches, one per class per "
+                    "64-step graph, timed over %d steps" % (job, loop_steps, PERSIST_CMP_STEPS))
     return res
 
 
