@@ -1884,7 +1884,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
         std::sort(scored.begin(), scored.end());
         const size_t top = std::min<size_t>(6, scored.size());
         for (size_t t = 0; t < top && rc == LB_OK; ++t) {
-            const double ms = time_candidate(cands[scored[t].second], kGraphBig, reps + 1);
+            const double ms = time_candidate(cands[scored[t].second], kGraphBig, reps + 3);
             if (ms < 0.0) {
                 if (rc == LB_OK) rc = LB_ERR_CUDA;
                 break;
