@@ -354,7 +354,8 @@ def run_capillary(lbf, torch, steps=None):
     """Capillary filling (Sec. VI) on the 1000 x 120 set-up in FP32: the
     whole job (obstacle step, the meniscus fitted every 500 steps) timed on
     the host clock, and the Washburn force-balance fit of the filled length
-    over the second half."""
+    over the second half.  The autotuner picks between a launch per step and
+    one persistent launch per graph of steps; both are timed."""
     import numpy as np
 
     c = lbinputs.CAPILLARY_1000x120
@@ -365,6 +366,8 @@ def run_capillary(lbf, torch, steps=None):
     fluid = int((sim.geometry() == 0).sum())
     y0 = (c["ny"] - c["ch_w"]) // 2
     ts, ls, ths = [], [], []
+    sim.autotune(reps=2)
+    chosen = sim.schedule()
     sim.step(2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -379,18 +382,25 @@ def run_capillary(lbf, torch, steps=None):
         ths.append(th)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    dt_steps = time_steps(sim, 2000, torch)
     st = sim.stats()
+
+    def per_mode(s, persist):
+        s.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=persist))
+        s.step(128)
+        return time_steps(s, 2000, torch)
+
+    dt_mode = {m: per_mode(sim, m) for m in (0, 1)}
+    dt_steps = dt_mode[chosen["persist"]]
     sim.close()
-    # latency floor of the same kernel: one CTA's tile (32 x 8 nodes with a
+    # latency floor of the same kernels: one CTA's tile (32 x 8 nodes with a
     # small block), stepped the same way; the capillary step cannot be faster
     tiny = lbf.Lattice(p, 32, 8)
     cls = np.zeros((8, 32), np.uint8)
     cls[2:5, 10:14] = 1
     tiny.set_geometry(cls, [0.0, 0.0])
     tiny.init_phi(np.zeros((8, 32)))
-    tiny.step(64)
-    dt_floor = time_steps(tiny, 2000, torch)
+    dt_floor_mode = {m: per_mode(tiny, m) for m in (0, 1)}
+    dt_floor = dt_floor_mode[chosen["persist"]]
     tiny.close()
     t = np.array(ts, float)
     l = np.array(ls)
@@ -410,11 +420,18 @@ def run_capillary(lbf, torch, steps=None):
                 l_final=float(l[-1]), theta_a_late=theta_a,
                 washburn_slope=slope, washburn_slope_theory=k_theory,
                 nonfinite=int(st["nonfinite"]),
-                note="obstacle path, one fused launch per step (the state stays in L2, so "
-                     "launch and L2 latency bound it: latency_floor_us is the same kernel on a "
-                     "single 32 x 8 tile); front by lb_meniscus every 500 steps; Washburn fit "
-                     "(nu_a - nu_b) l^2/2 + nu_b L l vs t over the second half, theory "
-                     "gamma w cos(theta_a) / 6")
+                launch="persistent" if chosen["persist"] else "per step",
+                per_step_launch_us=dt_mode[0] / 2000 * 1e6,
+                persistent_launch_us=dt_mode[1] / 2000 * 1e6,
+                latency_floor_per_step_launch_us=dt_floor_mode[0] / 2000 * 1e6,
+                latency_floor_persistent_us=dt_floor_mode[1] / 2000 * 1e6,
+                note="obstacle path (the state stays in L2, so launch, L2 and neighbour-wait "
+                     "latency bound it): the fused obstacle step as a launch per step, or as one "
+                     "cooperative launch per 64-step graph with each 32 x 8 tile waiting only "
+                     "for the tiles under its halo; the autotuner picks (launch); step_us is the "
+                     "pick, latency_floor_us the same launch form on a single 32 x 8 tile; "
+                     "front by lb_meniscus every 500 steps; Washburn fit (nu_a - nu_b) l^2/2 + "
+                     "nu_b L l vs t over the second half, theory gamma w cos(theta_a) / 6")
 
 
 BATCH_JOB_STEPS = 10000

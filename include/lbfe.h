@@ -316,8 +316,13 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  *               to finish the step before, not for the whole GPU.  Then
  *               ctas_per_sm[k] = 0 gives each class a share of the GPU in
  *               proportion to its rows (the classes, launched side by side,
- *               finish together); n >= 1 fixes n CTAs per SM.  A wait that
- *               gives up makes lb_step report LB_ERR_TIMEOUT.
+ *               finish together); n >= 1 fixes n CTAs per SM.  A domain
+ *               with obstacles (lb_set_geometry; any precision) likewise
+ *               runs its steps as one cooperative launch of one CTA per
+ *               tile, each tile waiting only for its neighbouring tiles,
+ *               when all its tiles fit the GPU at once (else one launch per
+ *               step).  A wait that gives up makes lb_step report
+ *               LB_ERR_TIMEOUT.
  *  fill_pct:    persistent schedules: the shared-out CTAs of all classes
  *               fill this percentage of the GPU's registers, shared memory
  *               and thread slots (0 = 100; above 100 some CTAs wait for
@@ -332,7 +337,7 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  * Results do not depend on the schedule (bit for bit).  A single-domain
  * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
  * Errors: LB_ERR_INVALID_ARG for a value out of range, max_nx not
- * increasing, persist without compact FP32 storage, fill_pct outside
+ * increasing, persist on a batch without compact FP32 storage, fill_pct outside
  * [0, 400], or a seal_edges value not 0 or 1. */
 #define LB_MAX_SCHED_CLASSES 8
 typedef struct lb_schedule {

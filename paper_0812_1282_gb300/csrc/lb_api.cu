@@ -74,6 +74,7 @@ struct Layout {
     std::vector<size_t> dom_off;  // offset of domain d's buffer 0 (buffer 1 follows)
     std::vector<size_t> dom_bytes;  // bytes of one ping-pong buffer of domain d
     std::vector<size_t> geo_off;    // domain d's obstacle map (nx*ny bytes)
+    std::vector<size_t> geo_flags;  // its persistent step's tile flags and counter (ints)
     size_t flags = 0, dep_off = 0, dep_idx = 0;  // persistent schedules (batches)
     size_t descs = 0, items = 0, partials = 0, stats = 0, pts = 0, count = 0, staging = 0, err = 0,
            sched = 0;
@@ -102,6 +103,8 @@ bool build_layout(int precision, int n_dom, const int* nx, const int* ny, Layout
         const size_t nodes = size_t(nx[d]) * size_t(ny[d]);
         L.geo_off.push_back(off);
         off = align_up(off + nodes, kAlign);
+        L.geo_flags.push_back(off);
+        off = align_up(off + sizeof(int) * (size_t(lbfe::geo_tiles(nx[d], ny[d])) + 1), kAlign);
         max_nodes = std::max(max_nodes, (long long)nx[d] * ny[d]);
         max_nx = std::max<long long>(max_nx, nx[d]);
         // at most ceil(nx / 28) strips per row (the narrowest strip of any
@@ -513,17 +516,42 @@ long long launches_per_step(const lb_handle* h)
     return n + h->n_geo;  // one launch per domain with obstacles
 }
 
+// A domain with obstacles steps as one persistent launch per lb_step call
+// (each graph of steps) when the schedule asks for it and all its tiles fit
+// the GPU at once (a cooperative launch), else one launch per step.
+bool geo_persistent(const lb_handle* h, const DomDesc& D)
+{
+    if (!h->sched.persist || !D.cls) return false;
+    const int occ = lbfe::geo_persist_occupancy(h->precision, h->coll);
+    return (long long)lbfe::geo_tiles(D.nx, D.ny) <= (long long)occ * h->sm_count;
+}
+
+// `len` steps of every domain with obstacles on `s`.
+int enqueue_geo_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStream_t s)
+{
+    if (h->n_geo == 0) return LB_OK;
+    for (int d = 0; d < h->n_dom; ++d) {
+        const DomDesc& D = h->descs[d];
+        if (!D.cls) continue;
+        int e = 0;
+        if (geo_persistent(h, D)) {
+            int* flags = reinterpret_cast<int*>(h->base + h->L.geo_flags[d]);
+            e = lbfe::launch_geo_persist(h->precision, h->coll, D, parity, fixed_parity ? 0 : 1, len,
+                                         flags, flags + lbfe::geo_tiles(D.nx, D.ny), s);
+        } else {
+            for (int k = 0; k < len && e == 0; ++k)
+                e = lbfe::launch_geo_step(h->precision, h->coll, D,
+                                          fixed_parity ? parity : parity ^ (k & 1), s);
+        }
+        if (e != 0)
+            return fail(LB_ERR_CUDA, "obstacle step launch failed: %s", cudaGetErrorString(cudaError_t(e)));
+    }
+    return LB_OK;
+}
+
 int enqueue_geo(lb_handle* h, int parity, cudaStream_t s)
 {
-    if (h->n_geo > 0)
-        for (const DomDesc& D : h->descs) {
-            if (!D.cls) continue;
-            const int e = lbfe::launch_geo_step(h->precision, h->coll, D, parity, s);
-            if (e != 0)
-                return fail(LB_ERR_CUDA, "obstacle step launch failed: %s",
-                            cudaGetErrorString(cudaError_t(e)));
-        }
-    return LB_OK;
+    return enqueue_geo_steps(h, 1, parity, false, s);
 }
 
 // One time step of every domain: the staged kernel for the domains without
@@ -562,8 +590,11 @@ int active_classes(const lb_handle* h)
 // steps in one launch).
 long long launches_for(const lb_handle* h, int len)
 {
-    if (!persistent(h)) return len * launches_per_step(h);
-    return active_classes(h) + (long long)len * h->n_geo;
+    long long geo = 0;
+    for (const DomDesc& D : h->descs)
+        if (D.cls) geo += geo_persistent(h, D) ? 1 : len;
+    if (!persistent(h)) return len * (launches_per_step(h) - h->n_geo) + geo;
+    return active_classes(h) + geo;
 }
 
 // Enqueue `len` steps on `s` (the capture stream).  With several schedule
@@ -591,13 +622,11 @@ int enqueue_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStre
             const int rc = class_steps(c, s);
             if (rc != LB_OK) return rc;
         }
-        for (int k = 0; k < len; ++k) {
-            const int rc = enqueue_geo(h, par(k), s);
-            if (rc != LB_OK) return rc;
-        }
-        return LB_OK;
+        return enqueue_geo_steps(h, len, parity, fixed_parity, s);
     }
     if (!(h->sched.chains && active_classes(h) > 1)) {
+        // a single domain with obstacles: its steps, maybe in one launch
+        if (h->n_dom == 1 && h->descs[0].cls) return enqueue_geo_steps(h, len, parity, fixed_parity, s);
         for (int k = 0; k < len; ++k) {
             const int rc = enqueue_step(h, par(k), s);
             if (rc != LB_OK) return rc;
@@ -621,8 +650,8 @@ int enqueue_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStre
         if (used > 0) LB_CUDA(cudaEventRecord(h->join_ev[used - 1], sc));
         ++used;
     }
-    for (int k = 0; k < len; ++k) {
-        const int rc = enqueue_geo(h, par(k), s);
+    {
+        const int rc = enqueue_geo_steps(h, len, parity, fixed_parity, s);
         if (rc != LB_OK) return rc;
     }
     for (int u = 1; u < used; ++u) LB_CUDA(cudaStreamWaitEvent(s, h->join_ev[u - 1], 0));
@@ -1817,11 +1846,19 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     if (reps < 1) reps = 1;
     int max_ny = 0;
     for (auto& D : h->descs) max_ny = std::max(max_ny, D.ny);
-    // with obstacles only, no domain uses the staged kernel: nothing to tune
+    // with obstacles only, no domain uses the staged kernel; a single domain
+    // with obstacles chooses between per-step and persistent launches
     const bool plain = h->n_dom == 1 ? h->descs[0].cls == nullptr : h->n_items > 0;
     std::vector<lb_schedule> cands;
     if (!plain) {
         cands.push_back(h->sched);
+        if (h->n_dom == 1) {
+            // one domain with obstacles: a launch per step, or its steps in
+            // one persistent launch
+            lb_schedule p = h->sched;
+            p.persist = !p.persist;
+            cands.push_back(p);
+        }
     } else if (h->n_dom > 1) {
         cands = batch_candidates(h);
     } else {
@@ -1852,7 +1889,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     // one timing of a candidate (ms per step); negative on failure
     auto time_candidate = [&](const lb_schedule& c, int len, int r) -> double {
         if ((rc = lb_set_schedule(h, &c)) != LB_OK) return -1.0;
-        if (h->n_dom > 1) return time_graph_steps(h, len, r, e0, e1);
+        if (h->n_dom > 1 || !plain) return time_graph_steps(h, len, r, e0, e1);
         // warm-up, then time `r` launches that read the current buffer and
         // write the idle one (the state itself does not advance)
         if ((rc = enqueue_step(h, h->parity, h->stream)) != LB_OK) return -1.0;
@@ -1880,7 +1917,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
         }
         scored.emplace_back(ms, k);
     }
-    if (rc == LB_OK && h->n_dom > 1 && scored.size() > 1) {
+    if (rc == LB_OK && (h->n_dom > 1 || !plain) && scored.size() > 1) {
         std::sort(scored.begin(), scored.end());
         const size_t top = std::min<size_t>(6, scored.size());
         for (size_t t = 0; t < top && rc == LB_OK; ++t) {

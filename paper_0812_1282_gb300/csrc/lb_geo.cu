@@ -45,6 +45,7 @@
 // phi field instead of a phi pass through memory.
 #include <cuda_runtime.h>
 
+#include "lb_async.cuh"
 #include "lb_internal.h"
 #include "lb_node.cuh"
 
@@ -129,26 +130,27 @@ __device__ __forceinline__ int wrap_any(int v, int n)
     return r < 0 ? r + n : r;
 }
 
-template <typename Real, bool MRT>
-__global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int parity)
+// Per-CTA tables of a tile: the wrapped halo coordinates and the class map
+// with its halo.  They depend only on the geometry, so the persistent form
+// builds them once per launch.
+struct GeoTables {
+    int colx[kGCX];  // wrapped column (+ kXOff) of each halo column
+    int rowo[kGCY];  // offset of each halo row (wrapped row x pitch)
+    int rowc[kGCY];  // the same row in the class map (wrapped row x nx)
+    signed char cl[kGCY][kGCX];  // 0 fluid, k > 0 solid class k, -1 / -2 wall rows
+};
+
+__device__ __forceinline__ void geo_tile_setup(const DomDesc& D, int x0, int y0, GeoTables& t)
 {
-    __shared__ signed char cl[kGCY][kGCX];
-    __shared__ Real ph[kGPY][kGPX];
-    __shared__ int colx[kGCX];  // wrapped column (+ kXOff) of each halo column
-    __shared__ int rowo[kGCY];  // offset of each halo row (wrapped row x pitch)
-    __shared__ int rowc[kGCY];  // the same row in the class map (wrapped row x nx)
-    const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
     const int nx = D.nx, ny = D.ny;
-    const Real* fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
-    const Real* gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
-    // 0. periodic wrap of the halo coordinates, once per CTA
+    // 0. periodic wrap of the halo coordinates
     for (int k = threadIdx.x; k < kGCX + kGCY; k += blockDim.x) {
         if (k < kGCX)
-            colx[k] = wrap_any(x0 - kGC + k, nx) + kXOff;
+            t.colx[k] = wrap_any(x0 - kGC + k, nx) + kXOff;
         else {
             const int wy = wrap_any(y0 - kGC + (k - kGCX), ny);
-            rowo[k - kGCX] = wy * D.pitch;
-            rowc[k - kGCX] = wy * nx;
+            t.rowo[k - kGCX] = wy * D.pitch;
+            t.rowc[k - kGCX] = wy * nx;
         }
     }
     __syncthreads();
@@ -162,19 +164,43 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
         else if (D.walls && y >= ny)
             c = -2;
         else
-            c = D.cls[rowc[cy] + (colx[cx] - kXOff)];
-        cl[cy][cx] = static_cast<signed char>(c);
+            c = D.cls[t.rowc[cy] + (t.colx[cx] - kXOff)];
+        t.cl[cy][cx] = static_cast<signed char>(c);
     }
     __syncthreads();
+}
+
+// Load of a stored population: through L1, or (L2ONLY, the persistent form,
+// whose neighbours rewrite the state within the launch) from L2.
+template <bool L2ONLY, typename Real>
+__device__ __forceinline__ Real geo_ld(const Real* p)
+{
+    if constexpr (L2ONLY)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// One time step of the tile at (x0, y0): phi of the tile and its halo into
+// ph, then the tile's fluid and wall nodes.  Every thread of the CTA calls it
+// (it holds CTA barriers); threads without a node of their own only help
+// with phi.
+template <typename Real, bool MRT, bool L2ONLY>
+__device__ __forceinline__ void geo_tile_step(const DomDesc& D, int parity, int x0, int y0,
+                                              const GeoTables& t, Real (&ph)[kGPY][kGPX])
+{
+    const int nx = D.nx, ny = D.ny;
+    const Real* fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
+    const Real* gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
     // lattice coordinates (unwrapped, within the halos) to shared memory
-    auto cls_l = [&](int x, int y) -> int { return cl[y - y0 + kGC][x - x0 + kGC]; };
+    auto cls_l = [&](int x, int y) -> int { return t.cl[y - y0 + kGC][x - x0 + kGC]; };
     // a population pulled from a solid node bounces back (wall nodes stream)
     auto solid_l = [&](int x, int y) {
         const int c = cls_l(x, y);
         return c != 0 && c != kNodeWall;
     };
     auto phi_l = [&](int x, int y) -> Real { return ph[y - y0 + kGH][x - x0 + kGH]; };
-    auto off_l = [&](int x, int y) -> int { return rowo[y - y0 + kGC] + colx[x - x0 + kGC]; };
+    auto off_l = [&](int x, int y) -> int { return t.rowo[y - y0 + kGC] + t.colx[x - x0 + kGC]; };
     // the nine pulled values of fluid node (x, y) from population set src;
     // a solid source bounces back (the node's own reversed population)
     const long long P = D.plane;
@@ -184,15 +210,16 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
         for (int i = 0; i < 9; ++i) {
             const int sx = x - gex(i), sy = y - gey(i);
             if (i != 0 && solid_l(sx, sy))
-                v[i] = src[gopp(i) * P + own];
+                v[i] = geo_ld<L2ONLY>(src + gopp(i) * P + own);
             else
-                v[i] = src[i * P + off_l(sx, sy)];
+                v[i] = geo_ld<L2ONLY>(src + i * P + off_l(sx, sy));
         }
     };
-    const int xq = x0 + int(threadIdx.x) % kGTX, yq = y0 + int(threadIdx.x) / kGTX;
-    const bool live = xq < nx && yq < ny && (cls_l(xq, yq) == 0 || cls_l(xq, yq) == kNodeWall);
-    Real fpre[9];
-    if (live) pull(fs, xq, yq, fpre);
+    const int x = x0 + int(threadIdx.x) % kGTX, y = y0 + int(threadIdx.x) / kGTX;
+    const int cme = (x < nx && y < ny) ? cls_l(x, y) : 1;
+    const bool live = cme == 0 || cme == kNodeWall;
+    Real f[9];
+    if (live) pull(fs, x, y, f);
     // 2. phi of the tile and its halo (solid nodes: unused); a fixed trip
     // count lets the loads of all of a thread's positions be in flight at once
     constexpr int kPhiIters = (kGPX * kGPY + kGTX * kGTY - 1) / (kGTX * kGTY);
@@ -201,27 +228,22 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
         const int k = int(threadIdx.x) + it * kGTX * kGTY;
         if (k >= kGPX * kGPY) break;
         const int py = k / kGPX, px = k - py * kGPX;
-        const int x = x0 - kGH + px, y = y0 - kGH + py;
+        const int hx = x0 - kGH + px, hy = y0 - kGH + py;
         Real v = Real(0);
-        if (cls_l(x, y) == 0) {
+        if (cls_l(hx, hy) == 0) {
             Real g[9];
-            pull(gs, x, y, g);
+            pull(gs, hx, hy, g);
             v = phi_sum<Real>(g);
         }
         ph[py][px] = v;
     }
     __syncthreads();
     // 3. the tile's fluid and wall nodes
-    const int x = x0 + int(threadIdx.x) % kGTX, y = y0 + int(threadIdx.x) / kGTX;
-    if (x >= nx || y >= ny) return;
-    const int cme = cls_l(x, y);
-    if (cme != 0 && cme != kNodeWall) return;
+    if (!live) return;
     Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
     Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
     const int o = off_l(x, y);
-    Real f[9], g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = fpre[i];
+    Real g[9];
     pull(gs, x, y, g);
     if (cme == kNodeWall) {
         // node bounce-back: every population reversed, no collision
@@ -296,6 +318,96 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
     for (int i = 0; i < 9; ++i) {
         fd[i * P + o] = fo[i];
         gd[i * P + o] = go[i];
+    }
+}
+
+template <typename Real, bool MRT>
+__global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int parity)
+{
+    __shared__ GeoTables t;
+    __shared__ Real ph[kGPY][kGPX];
+    const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
+    geo_tile_setup(D, x0, y0, t);
+    geo_tile_step<Real, MRT, false>(D, parity, x0, y0, t, ph);
+}
+
+// Persistent multi-step form: a cooperative launch (every tile's CTA
+// resident at once) runs n_steps steps, one tile per CTA, step s reading
+// buffer parity0 ^ (s & flip).  Instead of a launch boundary per step, a tile
+// waits before step s until the tiles under its halo (kGC nodes around it,
+// periodic; usually its eight neighbours) have finished step s - 1: once
+// they are done with step s - 1 they are also done reading what step s
+// overwrites (the halo relation is symmetric).  A tile publishes its steps in
+// flags[tile] (steps done in this launch) after a CTA barrier and a fence;
+// neighbour data is read from L2 (the state changes within the launch).
+// The waits are bounded (flag_wait); a give-up stops the CTA at the next
+// step.  done[0] counts finished CTAs; the last one resets it and the flags.
+// (FP32: four CTAs per SM, so that a 1000 x 120 capillary's 480 tiles are
+// resident at once on 152 SMs.)
+template <typename Real, bool MRT>
+__global__ void __launch_bounds__(kGTX * kGTY, sizeof(Real) == 4 ? 4 : 2)
+    geo_persist_kernel(DomDesc D, int parity0, int flip, int n_steps, int* flags, int* done)
+{
+    __shared__ GeoTables t;
+    __shared__ Real ph[kGPY][kGPX];
+    __shared__ int nbr[16];
+    __shared__ int n_nbr, stop, last_cta;
+    const int ntx = int(gridDim.x), nty = int(gridDim.y);
+    const int tx = int(blockIdx.x), ty = int(blockIdx.y), me = ty * ntx + tx;
+    const int x0 = tx * kGTX, y0 = ty * kGTY;
+    geo_tile_setup(D, x0, y0, t);
+    if (threadIdx.x == 0) {
+        // the tiles under the halo (the wrapped columns and rows of the
+        // tables; a short last tile can bring a second tile within reach)
+        int cx[4], cy[4], ncx = 0, ncy = 0;
+        for (int k = 0; k < kGCX; ++k) {
+            const int q = (t.colx[k] - kXOff) / kGTX;
+            bool seen = false;
+            for (int j = 0; j < ncx; ++j) seen = seen || cx[j] == q;
+            if (!seen) cx[ncx++] = q;
+        }
+        for (int k = 0; k < kGCY; ++k) {
+            const int y = y0 - kGC + k;
+            if (D.walls && (y < 0 || y >= D.ny)) continue;  // wall rows: no data
+            const int q = t.rowc[k] / D.nx / kGTY;
+            bool seen = false;
+            for (int j = 0; j < ncy; ++j) seen = seen || cy[j] == q;
+            if (!seen) cy[ncy++] = q;
+        }
+        int n = 0;
+        for (int a = 0; a < ncy; ++a)
+            for (int b = 0; b < ncx; ++b) {
+                const int q = cy[a] * ntx + cx[b];
+                if (q != me) nbr[n++] = q;
+            }
+        n_nbr = n;
+        stop = 0;
+    }
+    __syncthreads();
+    for (int s = 0; s < n_steps; ++s) {
+        if (s > 0) {
+            if (int(threadIdx.x) < n_nbr && !flag_wait(flags + nbr[threadIdx.x], s, D.err)) stop = 1;
+            __syncthreads();
+            if (stop) break;
+        }
+        geo_tile_step<Real, MRT, true>(D, parity0 ^ (s & flip), x0, y0, t, ph);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(flags + me, s + 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_cta = atomicAdd(done, 1) == ntx * nty - 1;
+    }
+    __syncthreads();
+    if (last_cta) {
+        __threadfence();
+        for (int k = int(threadIdx.x); k < ntx * nty; k += int(blockDim.x)) flags[k] = 0;
+        if (threadIdx.x == 0) done[0] = 0;
+        __threadfence();
     }
 }
 
@@ -403,7 +515,56 @@ cudaError_t geo_step_t(const DomDesc& d, int parity, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename Real, bool MRT>
+cudaError_t geo_persist_t(const DomDesc& d, int parity0, int flip, int n_steps, int* flags,
+                          int* done, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((d.nx + kGTX - 1) / kGTX, (d.ny + kGTY - 1) / kGTY);
+    cfg.blockDim = dim3(kGTX * kGTY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, geo_persist_kernel<Real, MRT>, d, parity0, flip, n_steps, flags,
+                              done);
+}
+
+template <typename Real, bool MRT>
+int geo_persist_occupancy_t()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, geo_persist_kernel<Real, MRT>, kGTX * kGTY,
+                                                      0) != cudaSuccess)
+        return 0;
+    return n;
+}
+
 }  // namespace
+
+int geo_tiles(int nx, int ny) { return ((nx + kGTX - 1) / kGTX) * ((ny + kGTY - 1) / kGTY); }
+
+int geo_persist_occupancy(int precision, int coll)
+{
+    if (precision == 0)
+        return coll ? geo_persist_occupancy_t<float, true>() : geo_persist_occupancy_t<float, false>();
+    return coll ? geo_persist_occupancy_t<double, true>() : geo_persist_occupancy_t<double, false>();
+}
+
+int launch_geo_persist(int precision, int coll, const DomDesc& d, int parity0, int flip,
+                       int n_steps, int* flags, int* done, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_steps <= 0) return int(cudaErrorInvalidValue);
+    if (precision == 0)
+        return int(coll ? geo_persist_t<float, true>(d, parity0, flip, n_steps, flags, done, s)
+                        : geo_persist_t<float, false>(d, parity0, flip, n_steps, flags, done, s));
+    return int(coll ? geo_persist_t<double, true>(d, parity0, flip, n_steps, flags, done, s)
+                    : geo_persist_t<double, false>(d, parity0, flip, n_steps, flags, done, s));
+}
 
 int launch_geo_step(int precision, int coll, const DomDesc& d, int parity, void* stream)
 {

@@ -250,3 +250,74 @@ def test_small_obstacle_domains_match_oracle(lbf, orc, walls, nx, ny, block):
     assert max_diff(f[:, fl], ref.f[:, fl]) <= 1e-12
     assert max_diff(g[:, fl], ref.g[:, fl]) <= 1e-12
     sim.close()
+
+
+def _persistent_case(lbf, orc, prec, nx, ny, walls, make_cls, node_walls=False):
+    kw = dict(_kw(orc, "mrt"), walls=walls)
+    cls = make_cls(nx, ny)
+    hc = [0.0, orc.wetting_h(70.0), orc.wetting_h(110.0), 0.1]
+    phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 21)
+    out = []
+    for persist in (0, 1):
+        sim = lbf.Lattice(lbf.params(precision=prec, **kw), nx, ny)
+        sim.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=persist))
+        sim.set_geometry(cls, hc)
+        sim.init_phi(phi0)
+        sim.step(131)  # a 64-step graph twice, a 2-step graph and one single step
+        out.append(sim.populations())
+        sim.close()
+    return out
+
+
+def _blocks(nx, ny):
+    cls = np.zeros((ny, nx), np.uint8)
+    cls[2:6, 8:14] = 1
+    cls[ny - 7:ny - 3, nx // 2:nx // 2 + 5] = 2
+    cls[ny // 2 - 1:ny // 2 + 2, 3:6] = 3
+    return cls
+
+
+def _node_walls(nx, ny):
+    cls = np.zeros((ny, nx), np.uint8)
+    cls[0] = 8
+    cls[-1] = 8
+    cls[4:8, 8:14] = 1
+    cls[ny // 2 - 1:ny // 2 + 2, 30:36] = 2
+    return cls
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("nx,ny,walls,cls_fn", [
+    (40, 24, True, _blocks),
+    (97, 25, False, _blocks),    # short last tiles in x and y: halos reach two tiles on
+    (65, 17, False, _blocks),    # the far side of the periodic wrap
+    (13, 9, True, lambda nx, ny: _small(nx, ny)),
+    (200, 60, True, _node_walls),
+])
+def test_persistent_obstacle_steps_are_bitwise_equal(lbf, orc, prec, nx, ny, walls, cls_fn):
+    """One cooperative launch of all of a domain's tiles per graph of steps,
+    each tile waiting only for the tiles under its halo, gives the state of
+    a launch per step bit for bit: walls and periodic rows, tiles shorter
+    than the halo, node walls, FP32 and FP64."""
+    (f0, g0), (f1, g1) = _persistent_case(lbf, orc, prec, nx, ny, walls, cls_fn)
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+
+
+def _small(nx, ny):
+    cls = np.zeros((ny, nx), np.uint8)
+    cls[3:6, 4:7] = 1
+    return cls
+
+
+def test_capillary_autotune_keeps_state(lbf, orc):
+    """The autotuner of a domain with obstacles times a launch per step
+    against one persistent launch per graph and leaves the state alone."""
+    sim = lbf.Lattice(lbf.params(precision="fp32", collision="mrt", tau_alpha=1.0, tau_beta=0.6),
+                      300, 60)
+    sim.init_channel(100, 20, orc.wetting_h(60.0), 0.05)
+    sim.step(5)
+    before = sim.save_state()
+    sim.autotune(reps=1)
+    assert sim.save_state() == before
+    assert sim.schedule()["persist"] in (0, 1)
+    sim.close()
