@@ -14,6 +14,7 @@
 
 #include "../../include/lbfe.h"
 #include "lb_internal.h"
+#include "lb_geo_persist.h"
 #include "lb_node.cuh"
 
 using lbfe::DomDesc;

@@ -47,6 +47,7 @@
 
 #include "lb_async.cuh"
 #include "lb_internal.h"
+#include "lb_geo_persist.h"
 #include "lb_node.cuh"
 
 namespace lbfe {

@@ -127,14 +127,6 @@ int launch_geo_step(int precision, int coll, const DomDesc& d, int parity, void*
 int launch_geo_init_eq(int precision, const DomDesc& d, const double* phi0, int parity,
                        void* stream);
 int launch_geo_solid_rest(int precision, const DomDesc& d, int b, void* stream);
-// Persistent multi-step obstacle step (a cooperative launch of one CTA per
-// tile for n_steps steps, step s reading buffer parity0 ^ (s & flip));
-// flags: geo_tiles(nx, ny) ints, done: one int, all zero between launches.
-// geo_persist_occupancy: resident CTAs per SM (0 on error).
-int geo_tiles(int nx, int ny);
-int geo_persist_occupancy(int precision, int coll);
-int launch_geo_persist(int precision, int coll, const DomDesc& d, int parity0, int flip,
-                       int n_steps, int* flags, int* done, void* stream);
 
 // Opt the step kernels in to large dynamic shared memory (call once per
 // device before the first launch, outside any stream capture).
