@@ -293,6 +293,9 @@ def _node_walls(nx, ny):
     (65, 17, False, _blocks),    # the far side of the periodic wrap
     (13, 9, True, lambda nx, ny: _small(nx, ny)),
     (200, 60, True, _node_walls),
+    # FP32: 480 tiles, all resident; FP64 (two CTAs per SM): too many, so a
+    # launch per step whatever the schedule says
+    (1000, 120, True, _blocks),
 ])
 def test_persistent_obstacle_steps_are_bitwise_equal(lbf, orc, prec, nx, ny, walls, cls_fn):
     """One cooperative launch of all of a domain's tiles per graph of steps,

@@ -77,6 +77,10 @@ def _schedules(lbf, compact):
                                                max_nx=[w(64)], chains=0, persist=1),
         # one CTA per SM: most items wait for a CTA to come free
         "multistep-few-ctas": lbf.schedule(64, 16, ctas_per_sm=1, persist=1),
+        # one- and two-row blocks in split strips: the most neighbours an item
+        # can wait for (five row blocks in three strips)
+        "multistep-single-rows": lbf.schedule([32, 64], [1, 2], ctas_per_sm=0, max_nx=[w(32)],
+                                              order=1, persist=1),
         # over-filled: some CTAs start only when a class finishes
         "multistep-overfilled-sealed": lbf.schedule([96, 160, 288], 32, ctas_per_sm=0,
                                                     max_nx=[w(96), w(160)], order=1,
@@ -88,7 +92,7 @@ def _schedules(lbf, compact):
 
 
 MULTISTEP = ("multistep-ladder", "multistep-short-blocks", "multistep-few-ctas",
-             "multistep-overfilled-sealed")
+             "multistep-overfilled-sealed", "multistep-single-rows")
 
 
 @pytest.mark.parametrize("name", ["one-class-persistent", "one-item-per-cta-largest-first",
