@@ -357,12 +357,14 @@ int lb_get_schedule(const lb_handle* h, lb_schedule* s);
 
 /* Autotuner: times each candidate for `reps` repetitions on the device
  * (without advancing the state) and keeps the fastest.  A single domain
- * tries launch shapes (block_x x rows).  A batch tries schedules
- * (lb_schedule): one class or two size classes with their own strip widths,
- * rows per work item, persistent or one-CTA-per-item grids, and the item
- * order, each timed as a captured graph of several steps.  Outputs (class
- * 0's shape and the best time per step in ms) may be NULL; lb_get_schedule
- * returns the whole choice. */
+ * tries launch shapes (block_x x rows); a single domain with obstacles, a
+ * launch per step against one persistent launch.  A batch tries schedules
+ * (lb_schedule): one class, or ladders of size classes with their own strip
+ * widths (sealed or not, per-step or persistent launches), rows per work
+ * item, persistent or one-CTA-per-item grids, and the item order, each
+ * timed as a captured graph of 16 steps, the fastest eight again over
+ * 64-step graphs.  Outputs (class 0's shape and the best time per step in
+ * ms) may be NULL; lb_get_schedule returns the whole choice. */
 int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms);
 
 /* Steps taken since the last initialisation (host-side count). */

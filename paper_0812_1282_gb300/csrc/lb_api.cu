@@ -1904,14 +1904,12 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
             return -1.0;
         return double(t) / r;
     };
-    // a batch: a few steps per graph (16 for a persistent schedule, whose
-    // launch fills and drains the GPU once per graph), so that chains and
-    // tails show; then the fastest few again over graphs of the length the
-    // steps run in (the short timings of neighbouring candidates are within
-    // noise)
+    // a batch: graphs of 16 steps, so that chains and tails show; then the
+    // fastest eight again over graphs of the length the steps run in (the
+    // leading candidates are within a few percent of each other)
     std::vector<std::pair<double, size_t>> scored;
     for (size_t k = 0; k < cands.size(); ++k) {
-        const double ms = time_candidate(cands[k], cands[k].persist ? 16 : 4, reps);
+        const double ms = time_candidate(cands[k], h->n_dom > 1 || !plain ? 16 : 4, reps);
         if (ms < 0.0) {
             if (rc == LB_OK) rc = LB_ERR_CUDA;
             break;
@@ -1920,7 +1918,7 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     }
     if (rc == LB_OK && (h->n_dom > 1 || !plain) && scored.size() > 1) {
         std::sort(scored.begin(), scored.end());
-        const size_t top = std::min<size_t>(6, scored.size());
+        const size_t top = std::min<size_t>(8, scored.size());
         for (size_t t = 0; t < top && rc == LB_OK; ++t) {
             const double ms = time_candidate(cands[scored[t].second], kGraphBig, reps + 3);
             if (ms < 0.0) {
