@@ -1,6 +1,6 @@
-// Persistent multi-step batched compact kernel (see lb_step_kernels.cuh),
+// Persistent multi-step batched compact kernel (see lb_step_persist.cuh),
 // in a translation unit of its own so that it compiles beside the others.
-#include "lb_step_kernels.cuh"
+#include "lb_step_persist.cuh"
 
 namespace lbfe {
 
