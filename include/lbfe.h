@@ -420,8 +420,8 @@ int lb_fp64_peak(int kind, void* stream, double* ops_per_s);
  * thread's current device is left as it was.  The scratch space is a fixed
  * device array of 1024 block partials (48 KiB) that the library carries on
  * every device it is loaded on until the process exits; its address is
- * looked up on the first call made on a device, so make that first call
- * before any stream capture.  All calls share that array: calls that may
+ * looked up (a runtime query) on the first call made on a device.  All
+ * calls share that array: calls that may
  * overlap on the GPU (unordered streams) race and can return wrong numbers.
  * At most LB_STATS_NOALLOC_MAX_VALUES population values per array
  * (9 * nx * ny); larger inputs, nx or ny < 1, NULL or non-device pointers,

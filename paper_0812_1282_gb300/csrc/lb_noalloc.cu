@@ -11,8 +11,8 @@
 // The array (kMaxBlocks block partials of kFields doubles, 48 KiB) is created
 // when the library is loaded on a device and lives until the process exits.
 // Its device address is looked up once per device, on the first call for
-// that device (the device holding the population arrays); make that first
-// call before any stream capture.  Every call shares the array: two calls
+// that device (the device holding the population arrays).  Every call
+// shares the array: two calls
 // whose kernels overlap on the GPU (different streams, no ordering between
 // them) race on it and may return wrong numbers; calls ordered on one
 // stream are safe.  Each call writes every slot it later reads, so nothing
