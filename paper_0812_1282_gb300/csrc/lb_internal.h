@@ -81,9 +81,11 @@ constexpr int kStatsFields = 6;
 // Launchers implemented in the .cu files.  All return a cudaError_t value
 // cast to int (0 = success) and enqueue on `stream`.
 // sched: two device ints, zero between launches (batched form only).
+// band_mul: single-domain form, the order in which row bands start (grid
+// row g takes band g band_mul mod the band count; 1 = in order).
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x,
-                int rows, int grid_persistent, int* sched, void* stream);
+                int rows, int band_mul, int grid_persistent, int* sched, void* stream);
 
 // One launch of the persistent multi-step batched compact kernel (FP32,
 // compact g storage) over one schedule class: items, dep_off (n_items + 1
@@ -134,19 +136,20 @@ int prepare_step_kernels();
 
 // Per-precision halves of launch_step / prepare_step_kernels.
 int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
-                    void* stream);
+                    int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
+                    int* sched, void* stream);
 int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
-                    void* stream);
+                    int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
+                    int* sched, void* stream);
 int prepare_step_f32();
 int prepare_step_f64();
 
-// Resident CTAs per SM of the batched step kernel for a launch shape (0 if
-// the shape is not supported or the query fails).
+// Resident CTAs per SM of the batched (single-domain) step kernel for a
+// launch shape (0 if the shape is not supported or the query fails).
 int step_batch_occupancy(int precision, int coll, int compact, int block_x);
-int batch_occupancy_f32(int coll, int compact, int bx);
-int batch_occupancy_f64(int coll, int bx);
+int step_single_occupancy(int precision, int coll, int compact, int block_x);
+int batch_occupancy_f32(int coll, int compact, int bx, int single);
+int batch_occupancy_f64(int coll, int bx, int single);
 
 // Dynamic shared memory of the step kernel for a block width (0 if the
 // width is not supported for this precision).

@@ -31,24 +31,34 @@ int prepare_step_kernels()
 
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x, int rows,
-                int grid_persistent, int* sched, void* stream)
+                int band_mul, int grid_persistent, int* sched, void* stream)
 {
     const bool ok = d.compact ? (block_x >= 32 && block_x <= 288 && block_x % 32 == 0)
                               : step_smem_bytes(precision, block_x) != 0;
     if (!ok) return int(cudaErrorInvalidValue);
     return precision == 0
                ? launch_step_f32(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
-                                 grid_persistent, sched, stream)
+                                 band_mul, grid_persistent, sched, stream)
                : launch_step_f64(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
-                                 grid_persistent, sched, stream);
+                                 band_mul, grid_persistent, sched, stream);
+}
+
+static int step_occupancy(int precision, int coll, int compact, int block_x, int single)
+{
+    if (compact ? (block_x < 32 || block_x > 288 || block_x % 32) : step_smem_bytes(precision, block_x) == 0)
+        return 0;
+    return precision == 0 ? batch_occupancy_f32(coll, compact, block_x, single)
+                          : batch_occupancy_f64(coll, block_x, single);
 }
 
 int step_batch_occupancy(int precision, int coll, int compact, int block_x)
 {
-    if (compact ? (block_x < 32 || block_x > 288 || block_x % 32) : step_smem_bytes(precision, block_x) == 0)
-        return 0;
-    return precision == 0 ? batch_occupancy_f32(coll, compact, block_x)
-                          : batch_occupancy_f64(coll, block_x);
+    return step_occupancy(precision, coll, compact, block_x, 0);
+}
+
+int step_single_occupancy(int precision, int coll, int compact, int block_x)
+{
+    return step_occupancy(precision, coll, compact, block_x, 1);
 }
 
 // Periodic ghost columns of every row of the 18 planes of one buffer, from

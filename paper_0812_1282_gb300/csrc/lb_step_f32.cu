@@ -4,24 +4,27 @@
 namespace lbfe {
 
 int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                    int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
-                    void* stream)
+                    int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
+                    int* sched, void* stream)
 {
     if (d.compact) {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         return int(coll ? launch_step_compact_w<true>(d, d_descs, d_items, n_items, n_dom, parity,
-                                                      bx, rows, grid_p, sched, s)
+                                                      bx, rows, band_mul, grid_p, sched, s)
                         : launch_step_compact_w<false>(d, d_descs, d_items, n_items, n_dom,
-                                                       parity, bx, rows, grid_p, sched, s));
+                                                       parity, bx, rows, band_mul, grid_p, sched, s));
     }
     return launch_step_prec<float>(coll, d, d_descs, d_items, n_items, n_dom, parity, bx, rows,
-                                   grid_p, sched, stream);
+                                   band_mul, grid_p, sched, stream);
 }
 
-int batch_occupancy_f32(int coll, int compact, int bx)
+int batch_occupancy_f32(int coll, int compact, int bx, int single)
 {
-    if (compact) return coll ? batch_occupancy_compact_w<true>(bx) : batch_occupancy_compact_w<false>(bx);
-    return coll ? batch_occupancy_w<float, true>(bx) : batch_occupancy_w<float, false>(bx);
+    if (compact)
+        return coll ? batch_occupancy_compact_w<true>(bx, single != 0)
+                    : batch_occupancy_compact_w<false>(bx, single != 0);
+    return coll ? batch_occupancy_w<float, true>(bx, single != 0)
+                : batch_occupancy_w<float, false>(bx, single != 0);
 }
 
 int prepare_step_f32()

@@ -24,15 +24,26 @@ constexpr int kComputeBarrierFull = 1;
 
 // Launch shape: blockDim.x = W + 32 (one producer warp, W / 32 compute
 // warps), W the strip width.
+// Row bands of a single-domain launch: the CTAs of grid row g take band
+// (g band_mul) mod gridDim.y (band_mul coprime to it, 1 = in order), so that
+// the host can make vertically adjacent bands start about one band's
+// duration apart: a band's first rows are then read while its lower
+// neighbour reads the same rows as its last, and come from L2.
+__device__ __forceinline__ int band_of(int band_mul)
+{
+    return band_mul > 1 ? int((long long)blockIdx.y * band_mul % gridDim.y) : int(blockIdx.y);
+}
+
 template <typename Real, bool MRT, int NWC>
-__global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity, int rows)
+__global__ void __launch_bounds__(288) step_single_kernel(DomDesc D, int parity, int rows,
+                                                          int band_mul)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStages<Real>;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages<Real, S, NWC>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
-    const int x0 = blockIdx.x * 32 * NW, y0 = blockIdx.y * rows;
+    const int x0 = blockIdx.x * 32 * NW, y0 = band_of(band_mul) * rows;
     unsigned q = 0;
     if (warp == 0) {
         produce_tile<Real, S, NWC>(D, parity, x0, y0, rows, smem, NW, q);
@@ -106,14 +117,15 @@ __global__ void __launch_bounds__(288) step_batch_kernel(const DomDesc* __restri
 // Compact-g forms (FP32, tau_phi = 1; lb_step_compact.cuh).  Same launch
 // shapes and scheduling as above, with strips of compact_strip(bx) columns.
 template <bool MRT, int NWC>
-__global__ void __launch_bounds__(320) step_single_compact_kernel(DomDesc D, int parity, int rows)
+__global__ void __launch_bounds__(320) step_single_compact_kernel(DomDesc D, int parity, int rows,
+                                                                  int band_mul)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int S = kStagesC;
     const int NW = NWC > 0 ? NWC : int(blockDim.x >> 5) - 1;
     init_stages_c<S>(smem, NW);
     const int warp = int(threadIdx.x >> 5);
-    const int x0 = blockIdx.x * compact_strip(32 * NW), y0 = blockIdx.y * rows;
+    const int x0 = blockIdx.x * compact_strip(32 * NW), y0 = band_of(band_mul) * rows;
     unsigned q = 0;
     if (warp == 0) {
         produce_tile_c<S, NWC>(D, parity, x0, y0, rows, 0, smem, NW, q);
@@ -189,14 +201,15 @@ __global__ void __maxnreg__(96)
 template <bool MRT, int NWC>
 cudaError_t launch_step_compact_t(const DomDesc& d, const DomDesc* d_descs,
                                   const WorkItem* d_items, int n_items, int n_dom, int parity,
-                                  int bx, int rows, int grid_p, int* sched, cudaStream_t s)
+                                  int bx, int rows, int band_mul, int grid_p, int* sched, cudaStream_t s)
 {
     const size_t smem = StageLayoutC(bx / 32, kStagesC).total();
     const int threads = bx + 32;
     if (n_dom == 1 && d_items == nullptr) {
         const int w = compact_strip(bx);
         dim3 grid((d.nx + w - 1) / w, (d.ny + rows - 1) / rows);
-        step_single_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows);
+        step_single_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows,
+                                                                        band_mul);
     } else {
         const int grid = grid_p > 0 ? grid_p : n_items;
         step_batch_compact_kernel<MRT, NWC><<<grid, threads, smem, s>>>(d_descs, d_items, n_items,
@@ -207,14 +220,14 @@ cudaError_t launch_step_compact_t(const DomDesc& d, const DomDesc* d_descs,
 
 template <typename Real, bool MRT, int NWC>
 cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                          int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
+                          int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
                           int* sched, cudaStream_t s)
 {
     const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
     const int threads = bx + 32;
     if (n_dom == 1 && d_items == nullptr) {
         dim3 grid((d.nx + bx - 1) / bx, (d.ny + rows - 1) / rows);
-        step_single_kernel<Real, MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows);
+        step_single_kernel<Real, MRT, NWC><<<grid, threads, smem, s>>>(d, parity, rows, band_mul);
     } else {
         const int grid = grid_p > 0 ? grid_p : n_items;
         step_batch_kernel<Real, MRT, NWC><<<grid, threads, smem, s>>>(d_descs, d_items, n_items,
@@ -226,107 +239,112 @@ cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkIt
 template <bool MRT>
 cudaError_t launch_step_compact_w(const DomDesc& d, const DomDesc* d_descs,
                                   const WorkItem* d_items, int n_items, int n_dom, int parity,
-                                  int bx, int rows, int grid_p, int* sched, cudaStream_t s)
+                                  int bx, int rows, int band_mul, int grid_p, int* sched, cudaStream_t s)
 {
     switch (bx) {
         case 32:
             return launch_step_compact_t<MRT, 1>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
         case 96:
             return launch_step_compact_t<MRT, 3>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
         case 64:
             return launch_step_compact_t<MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
         case 128:
             return launch_step_compact_t<MRT, 4>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
         case 256:
             return launch_step_compact_t<MRT, 8>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
         default:
             return launch_step_compact_t<MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s);
+                                                 rows, band_mul, grid_p, sched, s);
     }
 }
 
 template <typename Real, bool MRT>
 cudaError_t launch_step_w(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                          int n_items, int n_dom, int parity, int bx, int rows, int grid_p,
+                          int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
                           int* sched, cudaStream_t s)
 {
     switch (bx) {
         case 64:
             return launch_step_t<Real, MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                               rows, grid_p, sched, s);
+                                               rows, band_mul, grid_p, sched, s);
         case 128:
             return launch_step_t<Real, MRT, 4>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                               rows, grid_p, sched, s);
+                                               rows, band_mul, grid_p, sched, s);
         case 256:
             return launch_step_t<Real, MRT, 8>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                               rows, grid_p, sched, s);
+                                               rows, band_mul, grid_p, sched, s);
         default:
             return launch_step_t<Real, MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                               rows, grid_p, sched, s);
+                                               rows, band_mul, grid_p, sched, s);
     }
 }
 
 template <typename Real>
 int launch_step_prec(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
-                     int n_items, int n_dom, int parity, int bx, int rows, int grid_p, int* sched,
-                     void* stream)
+                     int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
+                     int* sched, void* stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return int(coll ? launch_step_w<Real, true>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                rows, grid_p, sched, s)
+                                                rows, band_mul, grid_p, sched, s)
                     : launch_step_w<Real, false>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, grid_p, sched, s));
+                                                 rows, band_mul, grid_p, sched, s));
 }
 
-// Resident CTAs per SM of the batched kernels for a launch shape (0 on error).
+// Resident CTAs per SM of the batched kernels (single: of the single-domain
+// kernels) for a launch shape (0 on error).
 template <bool MRT, int NWC>
-int batch_occupancy_compact_t(int bx)
+int batch_occupancy_compact_t(int bx, bool single)
 {
     int n = 0;
     const size_t smem = StageLayoutC(bx / 32, kStagesC).total();
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_batch_compact_kernel<MRT, NWC>,
-                                                      bx + 32, smem) != cudaSuccess)
-        return 0;
-    return n;
+    const cudaError_t e =
+        single ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &n, step_single_compact_kernel<MRT, NWC>, bx + 32, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &n, step_batch_compact_kernel<MRT, NWC>, bx + 32, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 template <typename Real, bool MRT, int NWC>
-int batch_occupancy_t(int bx)
+int batch_occupancy_t(int bx, bool single)
 {
     int n = 0;
     const size_t smem = StageLayout<Real>(bx / 32, kStages<Real>).total();
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_batch_kernel<Real, MRT, NWC>,
-                                                      bx + 32, smem) != cudaSuccess)
-        return 0;
-    return n;
+    const cudaError_t e =
+        single ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &n, step_single_kernel<Real, MRT, NWC>, bx + 32, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &n, step_batch_kernel<Real, MRT, NWC>, bx + 32, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 template <bool MRT>
-int batch_occupancy_compact_w(int bx)
+int batch_occupancy_compact_w(int bx, bool single)
 {
     switch (bx) {
-        case 32: return batch_occupancy_compact_t<MRT, 1>(bx);
-        case 64: return batch_occupancy_compact_t<MRT, 2>(bx);
-        case 96: return batch_occupancy_compact_t<MRT, 3>(bx);
-        case 128: return batch_occupancy_compact_t<MRT, 4>(bx);
-        case 256: return batch_occupancy_compact_t<MRT, 8>(bx);
-        default: return batch_occupancy_compact_t<MRT, 0>(bx);
+        case 32: return batch_occupancy_compact_t<MRT, 1>(bx, single);
+        case 64: return batch_occupancy_compact_t<MRT, 2>(bx, single);
+        case 96: return batch_occupancy_compact_t<MRT, 3>(bx, single);
+        case 128: return batch_occupancy_compact_t<MRT, 4>(bx, single);
+        case 256: return batch_occupancy_compact_t<MRT, 8>(bx, single);
+        default: return batch_occupancy_compact_t<MRT, 0>(bx, single);
     }
 }
 
 template <typename Real, bool MRT>
-int batch_occupancy_w(int bx)
+int batch_occupancy_w(int bx, bool single)
 {
     switch (bx) {
-        case 64: return batch_occupancy_t<Real, MRT, 2>(bx);
-        case 128: return batch_occupancy_t<Real, MRT, 4>(bx);
-        case 256: return batch_occupancy_t<Real, MRT, 8>(bx);
-        default: return batch_occupancy_t<Real, MRT, 0>(bx);
+        case 64: return batch_occupancy_t<Real, MRT, 2>(bx, single);
+        case 128: return batch_occupancy_t<Real, MRT, 4>(bx, single);
+        case 256: return batch_occupancy_t<Real, MRT, 8>(bx, single);
+        default: return batch_occupancy_t<Real, MRT, 0>(bx, single);
     }
 }
 
