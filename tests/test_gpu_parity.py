@@ -195,6 +195,26 @@ def test_fp32_tile_independence(lbf):
     assert outs[0] == outs[1] == outs[2]
 
 
+@pytest.mark.parametrize("compact", [False, True], ids=["full-g", "compact-g"])
+def test_strided_band_order_gives_the_same_state(lbf, compact):
+    """A lattice wide and tall enough that the row bands of one launch start
+    in a strided order (more bands than a quarter of the resident CTAs per
+    strip) steps to the same state, bit for bit, as with one band per strip
+    (in order) and with other band heights."""
+    nx, ny = 4096, 512
+    kw = dict(collision="mrt", tau_alpha=1.5, tau_beta=0.6, precision="fp32", compact_g=compact,
+              h_bottom=lbf.lb_wetting_h(60.0))
+    outs = []
+    for bx, rows in [(128, 8), (128, 512), (64, 4), (128, 16)]:
+        sim = lbf.Lattice(lbf.params(**kw), nx, ny)
+        sim.set_tile(bx, rows)
+        sim.init_random(0.1, 77)
+        sim.step(30)
+        outs.append(sim.save_state())
+        sim.close()
+    assert all(o == outs[0] for o in outs[1:])
+
+
 # ---------------------------------------------------------- FP32
 @pytest.mark.parametrize("coll,taus,relax", [("bgk", (1.0, 1.0), False),
                                              ("mrt", (1.5, 0.6), False),
