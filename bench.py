@@ -384,13 +384,17 @@ def run_capillary(lbf, torch, steps=None):
     wall = time.perf_counter() - t0
     st = sim.stats()
 
-    def per_mode(s, persist):
-        s.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=persist))
+    # launch forms: 0 a launch per step, 1 one persistent launch per graph,
+    # 2 two steps per launch
+    def per_mode(s, mode):
+        s.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=int(mode == 1),
+                                    steps_per_launch=2 if mode == 2 else 1))
         s.step(128)
         return time_steps(s, 2000, torch)
 
-    dt_mode = {m: per_mode(sim, m) for m in (0, 1)}
-    dt_steps = dt_mode[chosen["persist"]]
+    mode_of = 1 if chosen["persist"] else (2 if chosen["steps_per_launch"] == 2 else 0)
+    dt_mode = {m: per_mode(sim, m) for m in (0, 1, 2)}
+    dt_steps = dt_mode[mode_of]
     sim.close()
     # latency floor of the same kernels: one CTA's tile (32 x 8 nodes with a
     # small block), stepped the same way; the capillary step cannot be faster
@@ -399,8 +403,8 @@ def run_capillary(lbf, torch, steps=None):
     cls[2:5, 10:14] = 1
     tiny.set_geometry(cls, [0.0, 0.0])
     tiny.init_phi(np.zeros((8, 32)))
-    dt_floor_mode = {m: per_mode(tiny, m) for m in (0, 1)}
-    dt_floor = dt_floor_mode[chosen["persist"]]
+    dt_floor_mode = {m: per_mode(tiny, m) for m in (0, 1, 2)}
+    dt_floor = dt_floor_mode[mode_of]
     tiny.close()
     t = np.array(ts, float)
     l = np.array(ls)
@@ -420,15 +424,18 @@ def run_capillary(lbf, torch, steps=None):
                 l_final=float(l[-1]), theta_a_late=theta_a,
                 washburn_slope=slope, washburn_slope_theory=k_theory,
                 nonfinite=int(st["nonfinite"]),
-                launch="persistent" if chosen["persist"] else "per step",
+                launch=("per step", "persistent", "two steps per launch")[mode_of],
                 per_step_launch_us=dt_mode[0] / 2000 * 1e6,
                 persistent_launch_us=dt_mode[1] / 2000 * 1e6,
+                two_step_launch_us=dt_mode[2] / 2000 * 1e6,
                 latency_floor_per_step_launch_us=dt_floor_mode[0] / 2000 * 1e6,
                 latency_floor_persistent_us=dt_floor_mode[1] / 2000 * 1e6,
+                latency_floor_two_step_us=dt_floor_mode[2] / 2000 * 1e6,
                 note="obstacle path (the state stays in L2, so launch, L2 and neighbour-wait "
-                     "latency bound it): the fused obstacle step as a launch per step, or as one "
+                     "latency bound it): the fused obstacle step as a launch per step, as one "
                      "cooperative launch per 64-step graph with each 32 x 8 tile waiting only "
-                     "for the tiles under its halo; the autotuner picks (launch); step_us is the "
+                     "for the tiles under its halo, or two steps per launch (each tile stepping "
+                     "a four-node halo first); the autotuner picks (launch); step_us is the "
                      "pick, latency_floor_us the same launch form on a single 32 x 8 tile; "
                      "front by lb_meniscus every 500 steps; Washburn fit (nu_a - nu_b) l^2/2 + "
                      "nu_b L l vs t over the second half, theory gamma w cos(theta_a) / 6")

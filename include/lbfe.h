@@ -327,6 +327,12 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  *               fill this percentage of the GPU's registers, shared memory
  *               and thread slots (0 = 100; above 100 some CTAs wait for
  *               room and start when a class finishes).
+ *  steps_per_launch: a single domain with obstacles (lb_set_geometry):
+ *               2 runs two steps per launch (each CTA steps its tile and a
+ *               four-node halo into shared memory, then its tile again; the
+ *               halo is computed redundantly, no launch sits between the
+ *               two steps); 0 or 1 one step per launch.  Ignored elsewhere
+ *               and under persist.
  *  seal_edges[k]: compact storage: 1 makes class k's strips that cover
  *               their whole domain also zero the padding and (stale) ghost
  *               columns that share a 32-byte sector with their rows' first
@@ -338,7 +344,8 @@ int lb_get_tile(const lb_handle* h, int* block_x, int* rows);
  * handle uses block_x[0] and rows[0] only.  Invalidates captured graphs.
  * Errors: LB_ERR_INVALID_ARG for a value out of range, max_nx not
  * increasing, persist on a batch without compact FP32 storage, fill_pct outside
- * [0, 400], or a seal_edges value not 0 or 1. */
+ * [0, 400], steps_per_launch outside [0, 2], or a seal_edges value not 0
+ * or 1. */
 #define LB_MAX_SCHED_CLASSES 8
 typedef struct lb_schedule {
     int n_class;
@@ -350,6 +357,7 @@ typedef struct lb_schedule {
     int chains;
     int persist;
     int fill_pct;
+    int steps_per_launch;
     int seal_edges[LB_MAX_SCHED_CLASSES];
 } lb_schedule;
 int lb_set_schedule(lb_handle* h, const lb_schedule* s);
@@ -358,7 +366,7 @@ int lb_get_schedule(const lb_handle* h, lb_schedule* s);
 /* Autotuner: times each candidate for `reps` repetitions on the device
  * (without advancing the state) and keeps the fastest.  A single domain
  * tries launch shapes (block_x x rows); a single domain with obstacles, a
- * launch per step against one persistent launch.  A batch tries schedules
+ * launch per step, two steps per launch and one persistent launch.  A batch tries schedules
  * (lb_schedule): one class, or ladders of size classes with their own strip
  * widths (sealed or not, per-step or persistent launches), rows per work
  * item, persistent or one-CTA-per-item grids, and the item order, each

@@ -84,7 +84,8 @@ class Schedule(ctypes.Structure):
         ("rows", ctypes.c_int * LB_MAX_SCHED_CLASSES),
         ("ctas_per_sm", ctypes.c_int * LB_MAX_SCHED_CLASSES),
         ("order", ctypes.c_int), ("chains", ctypes.c_int), ("persist", ctypes.c_int),
-        ("fill_pct", ctypes.c_int), ("seal_edges", ctypes.c_int * LB_MAX_SCHED_CLASSES),
+        ("fill_pct", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+        ("seal_edges", ctypes.c_int * LB_MAX_SCHED_CLASSES),
     ]
 
     def as_dict(self):
@@ -93,16 +94,18 @@ class Schedule(ctypes.Structure):
                 "block_x": list(self.block_x)[:n], "rows": list(self.rows)[:n],
                 "ctas_per_sm": list(self.ctas_per_sm)[:n], "order": self.order,
                 "chains": self.chains, "persist": self.persist, "fill_pct": self.fill_pct,
+                "steps_per_launch": self.steps_per_launch,
                 "seal_edges": list(self.seal_edges)[:n]}
 
 
 def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1, persist=0,
-             fill_pct=0, seal_edges=0) -> Schedule:
+             fill_pct=0, seal_edges=0, steps_per_launch=0) -> Schedule:
     """Schedule block; block_x, rows and ctas_per_sm are per class (an int
     applies to every class); max_nx gives the class limits (n_class - 1
     values); persist=1 runs each class's steps in one persistent launch
     (fill_pct: the share of the GPU its CTAs fill); seal_edges (per class)
-    =1 makes whole-domain strips write whole sectors."""
+    =1 makes whole-domain strips write whole sectors; steps_per_launch=2 steps a
+    single domain with obstacles twice per launch."""
     n = len(max_nx) + 1
 
     def per_class(v):
@@ -114,7 +117,7 @@ def schedule(block_x, rows, ctas_per_sm=8, max_nx=(), order=0, chains=1, persist
     return Schedule(n, arr(*(list(max_nx) + [0] * (LB_MAX_SCHED_CLASSES - len(max_nx)))),
                     arr(*per_class(block_x)), arr(*per_class(rows)), arr(*per_class(ctas_per_sm)),
                     int(order), int(chains), int(persist), int(fill_pct),
-                    arr(*per_class(seal_edges)))
+                    int(steps_per_launch), arr(*per_class(seal_edges)))
 
 
 def params(a=0.04, kappa=0.04, gamma_mob=0.1, tau_phi=1.0, tau_alpha=1.0, tau_beta=1.0,

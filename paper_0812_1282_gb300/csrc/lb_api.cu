@@ -568,6 +568,17 @@ bool geo_persistent(const lb_handle* h, const DomDesc& D)
     return (long long)lbfe::geo_tiles(D.nx, D.ny) <= (long long)occ * h->sm_count;
 }
 
+// A single domain with obstacles may run two steps per launch; each such
+// launch flips the current buffer once.
+bool geo_fused(const lb_handle* h)
+{
+    return h->n_dom == 1 && h->descs[0].cls && h->sched.steps_per_launch == 2 &&
+           !geo_persistent(h, h->descs[0]);
+}
+
+// Buffer flips of `len` steps (a two-step launch flips once).
+int buffer_flips(const lb_handle* h, int len) { return geo_fused(h) ? len / 2 + (len & 1) : len; }
+
 // `len` steps of every domain with obstacles on `s`.
 int enqueue_geo_steps(lb_handle* h, int len, int parity, bool fixed_parity, cudaStream_t s)
 {
@@ -580,6 +591,15 @@ int enqueue_geo_steps(lb_handle* h, int len, int parity, bool fixed_parity, cuda
             int* flags = reinterpret_cast<int*>(h->base + h->L.geo_flags[d]);
             e = lbfe::launch_geo_persist(h->precision, h->coll, D, parity, fixed_parity ? 0 : 1, len,
                                          flags, flags + lbfe::geo_tiles(D.nx, D.ny), s);
+        } else if (geo_fused(h)) {
+            // pairs of steps, then a single one for an odd count
+            const int pairs = len / 2;
+            for (int k = 0; k < pairs && e == 0; ++k)
+                e = lbfe::launch_geo_step2(h->precision, h->coll, D,
+                                           fixed_parity ? parity : parity ^ (k & 1), s);
+            if (e == 0 && (len & 1))
+                e = lbfe::launch_geo_step(h->precision, h->coll, D,
+                                          fixed_parity ? parity : parity ^ (pairs & 1), s);
         } else {
             for (int k = 0; k < len && e == 0; ++k)
                 e = lbfe::launch_geo_step(h->precision, h->coll, D,
@@ -634,7 +654,7 @@ long long launches_for(const lb_handle* h, int len)
 {
     long long geo = 0;
     for (const DomDesc& D : h->descs)
-        if (D.cls) geo += geo_persistent(h, D) ? 1 : len;
+        if (D.cls) geo += geo_persistent(h, D) ? 1 : (geo_fused(h) ? len / 2 + (len & 1) : len);
     if (!persistent(h)) return len * (launches_per_step(h) - h->n_geo) + geo;
     return active_classes(h) + geo;
 }
@@ -870,7 +890,8 @@ int make_handle(const lb_params* per_dom, const int* nx, const int* ny, int n_do
         lb_destroy(h);
         return rc;
     };
-    if ((e = cudaError_t(lbfe::prepare_step_kernels())) != cudaSuccess)
+    if ((e = cudaError_t(lbfe::prepare_step_kernels())) != cudaSuccess ||
+        (e = cudaError_t(lbfe::prepare_geo_step2())) != cudaSuccess)
         return bail(fail(LB_ERR_CUDA, "kernel setup failed: %s", cudaGetErrorString(e)));
     if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) !=
             cudaSuccess ||
@@ -1236,7 +1257,7 @@ int lb_step(lb_handle* h, int n)
             if (rc != LB_OK) return rc;
             LB_CUDA(cudaGraphLaunch(g, h->stream));
         }
-        if (len & 1) h->parity ^= 1;
+        if (buffer_flips(h, len) & 1) h->parity ^= 1;
         h->steps += len;
         h->launches += launches_for(h, len);
         n -= len;
@@ -1755,6 +1776,8 @@ int lb_set_schedule(lb_handle* h, const lb_schedule* sc)
         return fail(LB_ERR_INVALID_ARG, "order, chains and persist must be 0 or 1");
     if (sc->fill_pct < 0 || sc->fill_pct > 400)
         return fail(LB_ERR_INVALID_ARG, "fill_pct must be in [0, 400]");
+    if (sc->steps_per_launch < 0 || sc->steps_per_launch > 2)
+        return fail(LB_ERR_INVALID_ARG, "steps_per_launch must be 0, 1 or 2");
 
     if (sc->persist && h->n_dom > 1 && !(h->precision == LB_FP32 && h->descs[0].compact))
         return fail(LB_ERR_INVALID_ARG, "persistent schedules need compact FP32 storage");
@@ -1895,11 +1918,15 @@ int lb_autotune(lb_handle* h, int reps, int* block_x, int* rows, double* best_ms
     if (!plain) {
         cands.push_back(h->sched);
         if (h->n_dom == 1) {
-            // one domain with obstacles: a launch per step, or its steps in
-            // one persistent launch
-            lb_schedule p = h->sched;
-            p.persist = !p.persist;
-            cands.push_back(p);
+            // one domain with obstacles: a launch per step, two steps per
+            // launch, or its steps in one persistent launch
+            cands.clear();
+            for (int mode = 0; mode < 3; ++mode) {
+                lb_schedule p = h->sched;
+                p.persist = mode == 2;
+                p.steps_per_launch = mode == 1 ? 2 : 1;
+                cands.push_back(p);
+            }
         }
     } else if (h->n_dom > 1) {
         cands = batch_candidates(h);

@@ -182,6 +182,86 @@ __device__ __forceinline__ Real geo_ld(const Real* p)
         return *p;
 }
 
+// The step of one fluid or wall node (x, y) of class cme from its pulled
+// populations f, g: cls_l(x, y) reads the class map and phi_l(x, y) phi of
+// the same state around the node (lattice coordinates; ghost values at solid
+// neighbours reach three nodes away); fo, go receive the new populations.
+template <typename Real, bool MRT, class ClsF, class PhiF>
+__device__ __forceinline__ void geo_node_update(const DomDesc& D, int x, int y, int cme,
+                                                const Real (&f)[9], const Real (&g)[9], ClsF cls_l,
+                                                PhiF phi_l, Real (&fo)[9], Real (&go)[9])
+{
+    const int ny = D.ny;
+    if (cme == kNodeWall) {
+        // node bounce-back: every population reversed, no collision
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fo[i] = f[gopp(i)];
+            go[i] = g[gopp(i)];
+        }
+        return;
+    }
+    const Real c = phi_sum<Real>(g);
+    // wetting ghost value of solid node (sx, sy): the mean over the axis (or,
+    // through a corner only, the diagonal) directions d towards fluid of
+    // phi(s + k d) - k h, k = D.wet_k
+    auto ghost = [&](int sx, int sy) -> Real {
+        const int k = cls_l(sx, sy);
+        const Real h = k == -1 ? (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
+                     : k == -2 ? (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top))
+                               : class_h<Real>(D, k);
+        Real sum = Real(0);
+        int n = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int dx = j == 0 ? 1 : (j == 1 ? -1 : 0);
+            const int dy = j == 2 ? 1 : (j == 3 ? -1 : 0);
+            if (cls_l(sx + dx, sy + dy) == 0) {
+                sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
+                ++n;
+            }
+        }
+        if (n == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int dx = (j == 0 || j == 3) ? 1 : -1;
+                const int dy = (j == 0 || j == 2) ? 1 : -1;
+                if (cls_l(sx + dx, sy + dy) == 0) {
+                    sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
+                    ++n;
+                }
+            }
+        }
+        const Real mean = n == 1 ? sum : (n == 2 ? sum * Real(0.5) : (n == 3 ? div_const<3>(sum) : sum * Real(0.25)));
+        return mean - Real(D.wet_k) * h;
+    };
+    // phi at the eight neighbours; ghost values at solid ones
+    Real nb[9];
+    bool next_to_solid = false;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int qx = x + gex(i), qy = y + gey(i);
+        const int cq = cls_l(qx, qy);
+        if (cq == kNodeWall) {
+            // one-sided wetting value from the first fluid row
+            next_to_solid = true;
+            nb[i] = qy == 0 ? phi_l(qx, 1) - (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
+                            : phi_l(qx, ny - 2) - (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top));
+        } else if (cq != 0) {
+            next_to_solid = true;
+            nb[i] = ghost(qx, qy);
+        } else {
+            nb[i] = phi_l(qx, qy);
+        }
+    }
+    Real dx, dy, lap;
+    // order: centre, E, W, N, S, NE, NW, SE, SW
+    stencils<Real>(c, nb[1], nb[2], nb[3], nb[4], nb[5], nb[7], nb[8], nb[6], dx, dy, lap);
+    const NodeParams<Real> prm = geo_params<Real>(D);
+    collide<Real, MRT>(prm, f, g, c, dx, dy, lap, D.step2 != 0 && next_to_solid,
+                       D.step2_relax_j != 0, fo, go);
+}
+
 // One time step of the tile at (x0, y0): phi of the tile and its halo into
 // ph, then the tile's fluid and wall nodes.  Every thread of the CTA calls it
 // (it holds CTA barriers); threads without a node of their own only help
@@ -244,77 +324,9 @@ __device__ __forceinline__ void geo_tile_step(const DomDesc& D, int parity, int 
     Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
     Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
     const int o = off_l(x, y);
-    Real g[9];
+    Real g[9], fo[9], go[9];
     pull(gs, x, y, g);
-    if (cme == kNodeWall) {
-        // node bounce-back: every population reversed, no collision
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            fd[i * P + o] = f[gopp(i)];
-            gd[i * P + o] = g[gopp(i)];
-        }
-        return;
-    }
-    const Real c = phi_sum<Real>(g);
-    // wetting ghost value of solid node (sx, sy): the mean over the axis (or,
-    // through a corner only, the diagonal) directions d towards fluid of
-    // phi(s + k d) - k h, k = D.wet_k
-    auto ghost = [&](int sx, int sy) -> Real {
-        const int k = cls_l(sx, sy);
-        const Real h = k == -1 ? (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
-                     : k == -2 ? (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top))
-                               : class_h<Real>(D, k);
-        Real sum = Real(0);
-        int n = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int dx = j == 0 ? 1 : (j == 1 ? -1 : 0);
-            const int dy = j == 2 ? 1 : (j == 3 ? -1 : 0);
-            if (cls_l(sx + dx, sy + dy) == 0) {
-                sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
-                ++n;
-            }
-        }
-        if (n == 0) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int dx = (j == 0 || j == 3) ? 1 : -1;
-                const int dy = (j == 0 || j == 2) ? 1 : -1;
-                if (cls_l(sx + dx, sy + dy) == 0) {
-                    sum += phi_l(sx + D.wet_k * dx, sy + D.wet_k * dy);
-                    ++n;
-                }
-            }
-        }
-        const Real mean = n == 1 ? sum : (n == 2 ? sum * Real(0.5) : (n == 3 ? div_const<3>(sum) : sum * Real(0.25)));
-        return mean - Real(D.wet_k) * h;
-    };
-    // phi at the eight neighbours; ghost values at solid ones
-    Real nb[9];
-    bool next_to_solid = false;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const int qx = x + gex(i), qy = y + gey(i);
-        const int cq = cls_l(qx, qy);
-        if (cq == kNodeWall) {
-            // one-sided wetting value from the first fluid row
-            next_to_solid = true;
-            nb[i] = qy == 0 ? phi_l(qx, 1) - (sizeof(Real) == 4 ? Real(D.fh_bot) : Real(D.h_bot))
-                            : phi_l(qx, ny - 2) - (sizeof(Real) == 4 ? Real(D.fh_top) : Real(D.h_top));
-        } else if (cq != 0) {
-            next_to_solid = true;
-            nb[i] = ghost(qx, qy);
-        } else {
-            nb[i] = phi_l(qx, qy);
-        }
-    }
-    Real dx, dy, lap;
-    // order: centre, E, W, N, S, NE, NW, SE, SW
-    stencils<Real>(c, nb[1], nb[2], nb[3], nb[4], nb[5], nb[7], nb[8], nb[6], dx, dy, lap);
-    const NodeParams<Real> prm = geo_params<Real>(D);
-    Real fo[9], go[9];
-    collide<Real, MRT>(prm, f, g, c, dx, dy, lap, D.step2 != 0 && next_to_solid,
-                       D.step2_relax_j != 0, fo, go);
+    geo_node_update<Real, MRT>(D, x, y, cme, f, g, cls_l, phi_l, fo, go);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         fd[i * P + o] = fo[i];
@@ -330,6 +342,171 @@ __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int pa
     const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
     geo_tile_setup(D, x0, y0, t);
     geo_tile_step<Real, MRT, false>(D, parity, x0, y0, t, ph);
+}
+
+// Two steps per launch (temporal blocking; the state stays in L2, so a step
+// is bound by latency, and a launch costs about as much as a step): a CTA
+// computes step t on its tile and a kFH-node halo into shared memory, then
+// step t + 1 on the tile from there.  Step t + 1 pulls one node beyond the
+// tile and takes phi three nodes beyond it, whose g pulls reach one more:
+// kFH = 4.  Step t then needs phi of the state at t kFH + kGH nodes beyond
+// the tile and the class map one node further.  Halo nodes are computed by
+// several CTAs with the same arithmetic (geo_node_update), so the result is
+// bit-identical to two single steps.  Reads buffer `parity` and writes the
+// other one, which therefore holds step t + 2: the launch flips the handle's
+// buffer once.
+constexpr int kFH = 4;            // step-t output halo
+constexpr int kFP = kFH + kGH;    // phi halo of the state at t
+constexpr int kFC = kFP + 1;      // class-map halo
+constexpr int kFCX = kGTX + 2 * kFC, kFCY = kGTY + 2 * kFC;
+constexpr int kFPX = kGTX + 2 * kFP, kFPY = kGTY + 2 * kFP;
+constexpr int kFAX = kGTX + 2 * kFH, kFAY = kGTY + 2 * kFH;
+
+template <typename Real>
+struct GeoFused {
+    Real fa[9][kFAY][kFAX];  // step-t output on the tile and its kFH halo
+    Real ga[9][kFAY][kFAX];
+    Real ph0[kFPY][kFPX];    // phi of the state at t
+    Real ph1[kGPY][kGPX];    // phi of the state at t + 1
+    int colx[kFCX];
+    int rowo[kFCY];
+    int rowc[kFCY];
+    signed char cl[kFCY][kFCX];
+};
+
+template <typename Real, bool MRT>
+__global__ void __launch_bounds__(kGTX * kGTY) geo_step2_kernel(DomDesc D, int parity)
+{
+    extern __shared__ __align__(16) unsigned char geo_smem[];
+    GeoFused<Real>& S = *reinterpret_cast<GeoFused<Real>*>(geo_smem);
+    const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
+    const int nx = D.nx, ny = D.ny;
+    const int tid = int(threadIdx.x), nthr = int(blockDim.x);
+    // 0. wrapped halo coordinates and the class map on the tile + kFC
+    for (int k = tid; k < kFCX + kFCY; k += nthr) {
+        if (k < kFCX)
+            S.colx[k] = wrap_any(x0 - kFC + k, nx) + kXOff;
+        else {
+            const int wy = wrap_any(y0 - kFC + (k - kFCX), ny);
+            S.rowo[k - kFCX] = wy * D.pitch;
+            S.rowc[k - kFCX] = wy * nx;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < kFCX * kFCY; k += nthr) {
+        const int cy = k / kFCX, cx = k - cy * kFCX;
+        const int y = y0 - kFC + cy;
+        int c;
+        if (D.walls && y < 0)
+            c = -1;
+        else if (D.walls && y >= ny)
+            c = -2;
+        else
+            c = D.cls[S.rowc[cy] + (S.colx[cx] - kXOff)];
+        S.cl[cy][cx] = static_cast<signed char>(c);
+    }
+    __syncthreads();
+    auto cls_l = [&](int x, int y) -> int { return S.cl[y - y0 + kFC][x - x0 + kFC]; };
+    auto solid_l = [&](int x, int y) {
+        const int c = cls_l(x, y);
+        return c != 0 && c != kNodeWall;
+    };
+    auto off_l = [&](int x, int y) -> int { return S.rowo[y - y0 + kFC] + S.colx[x - x0 + kFC]; };
+    const long long P = D.plane;
+    const Real* fs = static_cast<const Real*>(parity ? D.f[1] : D.f[0]);
+    const Real* gs = static_cast<const Real*>(parity ? D.g[1] : D.g[0]);
+    // pulls from the state at t (global) and at t + 1 (shared); a solid
+    // source bounces back (the node's own reversed population)
+    auto pull_g = [&](const Real* src, int x, int y, Real (&v)[9]) {
+        const int own = off_l(x, y);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = x - gex(i), sy = y - gey(i);
+            v[i] = (i != 0 && solid_l(sx, sy)) ? src[gopp(i) * P + own] : src[i * P + off_l(sx, sy)];
+        }
+    };
+    auto pull_s = [&](const Real (&a)[9][kFAY][kFAX], int x, int y, Real (&v)[9]) {
+        const int ax = x - x0 + kFH, ay = y - y0 + kFH;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = x - gex(i), sy = y - gey(i);
+            v[i] = (i != 0 && solid_l(sx, sy)) ? a[gopp(i)][ay][ax]
+                                               : a[i][sy - y0 + kFH][sx - x0 + kFH];
+        }
+    };
+    // 1. phi of the state at t on the tile + kFP (fixed trip counts: the
+    // loads of all of a thread's positions can be in flight at once)
+    constexpr int kT = kGTX * kGTY;
+#pragma unroll
+    for (int it = 0; it < (kFPX * kFPY + kT - 1) / kT; ++it) {
+        const int k = tid + it * kT;
+        if (k >= kFPX * kFPY) break;
+        const int py = k / kFPX, px = k - py * kFPX;
+        const int x = x0 - kFP + px, y = y0 - kFP + py;
+        Real v = Real(0);
+        if (cls_l(x, y) == 0) {
+            Real g[9];
+            pull_g(gs, x, y, g);
+            v = phi_sum<Real>(g);
+        }
+        S.ph0[py][px] = v;
+    }
+    __syncthreads();
+    auto phi0_l = [&](int x, int y) -> Real { return S.ph0[y - y0 + kFP][x - x0 + kFP]; };
+    // 2. step t on the tile + kFH, into shared memory (solid nodes: unused)
+#pragma unroll
+    for (int it = 0; it < (kFAX * kFAY + kT - 1) / kT; ++it) {
+        const int k = tid + it * kT;
+        if (k >= kFAX * kFAY) break;
+        const int ay = k / kFAX, ax = k - ay * kFAX;
+        const int x = x0 - kFH + ax, y = y0 - kFH + ay;
+        const int cme = cls_l(x, y);
+        if (cme != 0 && cme != kNodeWall) continue;
+        Real f[9], g[9], fo[9], go[9];
+        pull_g(fs, x, y, f);
+        pull_g(gs, x, y, g);
+        geo_node_update<Real, MRT>(D, x, y, cme, f, g, cls_l, phi0_l, fo, go);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S.fa[i][ay][ax] = fo[i];
+            S.ga[i][ay][ax] = go[i];
+        }
+    }
+    __syncthreads();
+    // 3. phi of the state at t + 1 on the tile + kGH
+#pragma unroll
+    for (int it = 0; it < (kGPX * kGPY + kT - 1) / kT; ++it) {
+        const int k = tid + it * kT;
+        if (k >= kGPX * kGPY) break;
+        const int py = k / kGPX, px = k - py * kGPX;
+        const int x = x0 - kGH + px, y = y0 - kGH + py;
+        Real v = Real(0);
+        if (cls_l(x, y) == 0) {
+            Real g[9];
+            pull_s(S.ga, x, y, g);
+            v = phi_sum<Real>(g);
+        }
+        S.ph1[py][px] = v;
+    }
+    __syncthreads();
+    auto phi1_l = [&](int x, int y) -> Real { return S.ph1[y - y0 + kGH][x - x0 + kGH]; };
+    // 4. step t + 1 on the tile, to the other buffer
+    const int x = x0 + tid % kGTX, y = y0 + tid / kGTX;
+    if (x >= nx || y >= ny) return;
+    const int cme = cls_l(x, y);
+    if (cme != 0 && cme != kNodeWall) return;
+    Real f[9], g[9], fo[9], go[9];
+    pull_s(S.fa, x, y, f);
+    pull_s(S.ga, x, y, g);
+    geo_node_update<Real, MRT>(D, x, y, cme, f, g, cls_l, phi1_l, fo, go);
+    Real* fd = static_cast<Real*>(parity ? D.f[0] : D.f[1]);
+    Real* gd = static_cast<Real*>(parity ? D.g[0] : D.g[1]);
+    const int o = off_l(x, y);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fd[i * P + o] = fo[i];
+        gd[i * P + o] = go[i];
+    }
 }
 
 // Persistent multi-step form: a cooperative launch (every tile's CTA
@@ -517,6 +694,22 @@ cudaError_t geo_step_t(const DomDesc& d, int parity, cudaStream_t s)
 }
 
 template <typename Real, bool MRT>
+cudaError_t geo_step2_t(const DomDesc& d, int parity, cudaStream_t s)
+{
+    const dim3 grid((d.nx + kGTX - 1) / kGTX, (d.ny + kGTY - 1) / kGTY);
+    geo_step2_kernel<Real, MRT><<<grid, kGTX * kGTY, sizeof(GeoFused<Real>), s>>>(d, parity);
+    return cudaGetLastError();
+}
+
+template <typename Real, bool MRT>
+cudaError_t geo_step2_prepare()
+{
+    return cudaFuncSetAttribute(geo_step2_kernel<Real, MRT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sizeof(GeoFused<Real>)));
+}
+
+template <typename Real, bool MRT>
 cudaError_t geo_persist_t(const DomDesc& d, int parity0, int flip, int n_steps, int* flags,
                           int* done, cudaStream_t s)
 {
@@ -565,6 +758,23 @@ int launch_geo_persist(int precision, int coll, const DomDesc& d, int parity0, i
                         : geo_persist_t<float, false>(d, parity0, flip, n_steps, flags, done, s));
     return int(coll ? geo_persist_t<double, true>(d, parity0, flip, n_steps, flags, done, s)
                     : geo_persist_t<double, false>(d, parity0, flip, n_steps, flags, done, s));
+}
+
+int launch_geo_step2(int precision, int coll, const DomDesc& d, int parity, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == 0)
+        return int(coll ? geo_step2_t<float, true>(d, parity, s) : geo_step2_t<float, false>(d, parity, s));
+    return int(coll ? geo_step2_t<double, true>(d, parity, s) : geo_step2_t<double, false>(d, parity, s));
+}
+
+int prepare_geo_step2()
+{
+    const cudaError_t r[] = {geo_step2_prepare<float, false>(), geo_step2_prepare<float, true>(),
+                             geo_step2_prepare<double, false>(), geo_step2_prepare<double, true>()};
+    for (cudaError_t v : r)
+        if (v != cudaSuccess) return int(v);
+    return 0;
 }
 
 int launch_geo_step(int precision, int coll, const DomDesc& d, int parity, void* stream)

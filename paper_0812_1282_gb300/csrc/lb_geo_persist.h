@@ -1,4 +1,4 @@
-// Host entry points of the persistent multi-step obstacle step (lb_geo.cu).
+// Host entry points of the multi-step obstacle steps (lb_geo.cu).
 #pragma once
 
 #include "lb_internal.h"
@@ -13,5 +13,11 @@ int geo_tiles(int nx, int ny);
 int geo_persist_occupancy(int precision, int coll);
 int launch_geo_persist(int precision, int coll, const DomDesc& d, int parity0, int flip,
                        int n_steps, int* flags, int* done, void* stream);
+// Two steps of an obstacle domain in one launch (temporal blocking): reads
+// buffer `parity`, writes the other (which then holds the state two steps
+// on).  prepare_geo_step2 opts the kernel in to its shared memory (once per
+// device, outside any stream capture).
+int launch_geo_step2(int precision, int coll, const DomDesc& d, int parity, void* stream);
+int prepare_geo_step2();
 
 }  // namespace lbfe

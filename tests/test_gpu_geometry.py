@@ -258,9 +258,10 @@ def _persistent_case(lbf, orc, prec, nx, ny, walls, make_cls, node_walls=False):
     hc = [0.0, orc.wetting_h(70.0), orc.wetting_h(110.0), 0.1]
     phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 21)
     out = []
-    for persist in (0, 1):
+    for persist, spl in ((0, 1), (1, 1), (0, 2)):
         sim = lbf.Lattice(lbf.params(precision=prec, **kw), nx, ny)
-        sim.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=persist))
+        sim.set_schedule(lbf.schedule(128, 16, ctas_per_sm=0, persist=persist,
+                                      steps_per_launch=spl))
         sim.set_geometry(cls, hc)
         sim.init_phi(phi0)
         sim.step(131)  # a 64-step graph twice, a 2-step graph and one single step
@@ -299,11 +300,46 @@ def _node_walls(nx, ny):
 ])
 def test_persistent_obstacle_steps_are_bitwise_equal(lbf, orc, prec, nx, ny, walls, cls_fn):
     """One cooperative launch of all of a domain's tiles per graph of steps,
-    each tile waiting only for the tiles under its halo, gives the state of
-    a launch per step bit for bit: walls and periodic rows, tiles shorter
-    than the halo, node walls, FP32 and FP64."""
-    (f0, g0), (f1, g1) = _persistent_case(lbf, orc, prec, nx, ny, walls, cls_fn)
+    each tile waiting only for the tiles under its halo, and two steps per
+    launch (each tile stepping a four-node halo first) give the state of a
+    launch per step bit for bit: walls and periodic rows, tiles shorter than
+    the halo, node walls, FP32 and FP64."""
+    (f0, g0), (f1, g1), (f2, g2) = _persistent_case(lbf, orc, prec, nx, ny, walls, cls_fn)
     assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert np.array_equal(f0, f2) and np.array_equal(g0, g2)
+
+
+def test_two_step_launches_switched_midrun_keep_the_state(lbf, orc):
+    """A two-step launch flips the current buffer once: switching between
+    one and two steps per launch mid-run, odd step counts and a checkpoint
+    keep the run identical to one stepped a launch per step."""
+    nx, ny = 200, 60
+    kw = dict(_kw(orc, "mrt"), walls=True)
+    cls = _node_walls(nx, ny)
+    hc = [0.0, orc.wetting_h(70.0), orc.wetting_h(110.0)]
+    phi0 = lbinputs.smooth_random_field(nx, ny, 0.9, 33)
+    ref = lbf.Lattice(lbf.params(precision="fp32", **kw), nx, ny)
+    ref.set_geometry(cls, hc)
+    ref.init_phi(phi0)
+    ref.step(200)
+    sim = lbf.Lattice(lbf.params(precision="fp32", **kw), nx, ny)
+    sim.set_geometry(cls, hc)
+    sim.init_phi(phi0)
+    two = lbf.schedule(128, 16, ctas_per_sm=0, steps_per_launch=2)
+    one = lbf.schedule(128, 16, ctas_per_sm=0)
+    sim.set_schedule(two)
+    sim.step(67)
+    sim.set_schedule(one)
+    sim.step(3)
+    blob = sim.save_state()
+    sim.set_schedule(two)
+    sim.step(11)
+    sim.load_state(blob)
+    sim.step(130)
+    assert sim.step_count == ref.step_count == 200
+    assert sim.save_state()[32:] == ref.save_state()[32:]
+    sim.close()
+    ref.close()
 
 
 def _small(nx, ny):
