@@ -399,11 +399,13 @@ void persist_grids(lb_handle* h, const std::vector<WorkItem>& items)
 // them in L2.  Grid row g takes band g L^-1 mod B (B bands), L odd, coprime
 // to B and about 3/4 of N (measured on 8192^2 with 16-row bands, N = 17.9:
 // 63.4 GLUPS in order, 65.0 at L = 13, 64.5 at 17, 62.7 at 21 and beyond);
-// 1 (in order) when all bands are in flight at once.
+// 1 (in order) when all bands are in flight at once.  Compact storage only:
+// the full-storage step measured no gain at any L (43.9 GLUPS in order,
+// 42.8-44.1 strided).
 int band_multiplier(const lb_handle* h)
 {
     const DomDesc& D = h->descs[0];
-    if (D.cls || h->n_dom != 1) return 1;
+    if (D.cls || h->n_dom != 1 || !D.compact) return 1;
     const int bx = h->block_x(), rows = h->rows();
     const int w = D.compact ? lbfe::compact_strip(bx) : bx;
     const long long strips = (D.nx + w - 1) / w, B = (D.ny + rows - 1) / rows;
