@@ -454,13 +454,14 @@ def batch_params(lbf, specs, compact):
                        step2_relax_momentum=True, compact_g=compact) for s in specs]
 
 
-# The five-class ladder the autotuner picks for the 256 drops (strips of 184,
-# 308, 370, 432 and 556 columns, 64 rows): a fixed schedule for profiling runs.
-LADDER_BX = (96, 160, 192, 224, 288)
+# The eight-class ladder the autotuner picks for the 256 drops (strips of 120,
+# 184, 244, 308, 368, 432, 492 and 556 columns, 96 rows): a fixed schedule for
+# profiling runs.
+LADDER_BX = (64, 96, 128, 160, 192, 224, 256, 288)
 
 
 # fixed batched schedules (--schedule): (rows per item, persistent launches)
-FIXED_SCHEDULES = {"ladder": (64, 0), "ladder-persist": (32, 1)}
+FIXED_SCHEDULES = {"ladder": (96, 0), "ladder-persist": (32, 1)}
 
 
 def ladder_schedule(lbf, rows=64, persist=0):
@@ -611,7 +612,7 @@ def run_batched(lbf, torch, loop_steps=20, compact=False, ws=1, rank=0, job_step
                     "relaxing Step-2 reading; angle_err_max_deg = the timed run's angles "
                     "against the FP64 oracle's (tests/golden/batch_angles.json, 16 smallest "
                     "domains, compact and full storage both tested in "
-                    "tests/test_gpu_batch_angles.py); persistent_launches = the five-class "
+                    "tests/test_gpu_batch_angles.py); persistent_launches = the eight-class "
                     "ladder (32 rows) as persistent multi-step launches, one per class per "
                     "64-step graph, timed over %d steps" % (job, loop_steps, PERSIST_CMP_STEPS))
     return res
@@ -953,7 +954,7 @@ def main():
     ap.add_argument("--job-steps", type=int, default=None,
                     help="steps of the batched job (profiling aid; default 10000)")
     ap.add_argument("--schedule", choices=("auto", "ladder", "ladder-persist"), default="auto",
-                    help="batched job: autotuned schedule, or the fixed five-class ladder "
+                    help="batched job: autotuned schedule, or the fixed eight-class ladder "
                          "(one launch per class per step, or per class per graph of "
                          "persistent launches; profiling aid: no autotuning launches)")
     ap.add_argument("--experiment", choices=("ramp", "stripe"), default=None,

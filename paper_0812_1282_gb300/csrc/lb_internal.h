@@ -83,9 +83,14 @@ constexpr int kStatsFields = 6;
 // sched: two device ints, zero between launches (batched form only).
 // band_mul: single-domain form, the order in which row bands start (grid
 // row g takes band g band_mul mod the band count; 1 = in order).
+// one_body: batched form, launch the kernel built for any block width (the
+// warp count read from the block size) rather than the one built for this
+// width, so that the classes of a schedule, which run side by side, share
+// one code body in the SMs' instruction caches.
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x,
-                int rows, int band_mul, int grid_persistent, int* sched, void* stream);
+                int rows, int band_mul, int grid_persistent, int* sched, bool one_body,
+                void* stream);
 
 // One launch of the persistent multi-step batched compact kernel (FP32,
 // compact g storage) over one schedule class: items, dep_off (n_items + 1
@@ -137,10 +142,10 @@ int prepare_step_kernels();
 // Per-precision halves of launch_step / prepare_step_kernels.
 int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                     int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
-                    int* sched, void* stream);
+                    int* sched, bool one_body, void* stream);
 int launch_step_f64(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                     int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
-                    int* sched, void* stream);
+                    int* sched, bool one_body, void* stream);
 int prepare_step_f32();
 int prepare_step_f64();
 

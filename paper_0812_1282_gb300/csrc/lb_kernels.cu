@@ -31,16 +31,16 @@ int prepare_step_kernels()
 
 int launch_step(int precision, int coll, const DomDesc& d, const DomDesc* d_descs,
                 const WorkItem* d_items, int n_items, int n_dom, int parity, int block_x, int rows,
-                int band_mul, int grid_persistent, int* sched, void* stream)
+                int band_mul, int grid_persistent, int* sched, bool one_body, void* stream)
 {
     const bool ok = d.compact ? (block_x >= 32 && block_x <= 288 && block_x % 32 == 0)
                               : step_smem_bytes(precision, block_x) != 0;
     if (!ok) return int(cudaErrorInvalidValue);
     return precision == 0
                ? launch_step_f32(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
-                                 band_mul, grid_persistent, sched, stream)
+                                 band_mul, grid_persistent, sched, one_body, stream)
                : launch_step_f64(coll, d, d_descs, d_items, n_items, n_dom, parity, block_x, rows,
-                                 band_mul, grid_persistent, sched, stream);
+                                 band_mul, grid_persistent, sched, one_body, stream);
 }
 
 static int step_occupancy(int precision, int coll, int compact, int block_x, int single)

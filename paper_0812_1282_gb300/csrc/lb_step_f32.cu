@@ -5,17 +5,18 @@ namespace lbfe {
 
 int launch_step_f32(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                     int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
-                    int* sched, void* stream)
+                    int* sched, bool one_body, void* stream)
 {
     if (d.compact) {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         return int(coll ? launch_step_compact_w<true>(d, d_descs, d_items, n_items, n_dom, parity,
-                                                      bx, rows, band_mul, grid_p, sched, s)
+                                                      bx, rows, band_mul, grid_p, sched, one_body, s)
                         : launch_step_compact_w<false>(d, d_descs, d_items, n_items, n_dom,
-                                                       parity, bx, rows, band_mul, grid_p, sched, s));
+                                                       parity, bx, rows, band_mul, grid_p, sched,
+                                                       one_body, s));
     }
     return launch_step_prec<float>(coll, d, d_descs, d_items, n_items, n_dom, parity, bx, rows,
-                                   band_mul, grid_p, sched, stream);
+                                   band_mul, grid_p, sched, one_body, stream);
 }
 
 int batch_occupancy_f32(int coll, int compact, int bx, int single)

@@ -236,11 +236,19 @@ cudaError_t launch_step_t(const DomDesc& d, const DomDesc* d_descs, const WorkIt
     return cudaGetLastError();
 }
 
+// one_body: a batched launch takes the kernel built for any width (NW read
+// from the block size) instead of the one built for its own width.  The
+// classes of a schedule run side by side on the SMs, and with one body they
+// share the instruction caches.
 template <bool MRT>
 cudaError_t launch_step_compact_w(const DomDesc& d, const DomDesc* d_descs,
                                   const WorkItem* d_items, int n_items, int n_dom, int parity,
-                                  int bx, int rows, int band_mul, int grid_p, int* sched, cudaStream_t s)
+                                  int bx, int rows, int band_mul, int grid_p, int* sched,
+                                  bool one_body, cudaStream_t s)
 {
+    if (one_body && !(n_dom == 1 && d_items == nullptr))
+        return launch_step_compact_t<MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx,
+                                             rows, band_mul, grid_p, sched, s);
     switch (bx) {
         case 32:
             return launch_step_compact_t<MRT, 1>(d, d_descs, d_items, n_items, n_dom, parity, bx,
@@ -266,8 +274,11 @@ cudaError_t launch_step_compact_w(const DomDesc& d, const DomDesc* d_descs,
 template <typename Real, bool MRT>
 cudaError_t launch_step_w(const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                           int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
-                          int* sched, cudaStream_t s)
+                          int* sched, bool one_body, cudaStream_t s)
 {
+    if (one_body && !(n_dom == 1 && d_items == nullptr))
+        return launch_step_t<Real, MRT, 0>(d, d_descs, d_items, n_items, n_dom, parity, bx, rows,
+                                           band_mul, grid_p, sched, s);
     switch (bx) {
         case 64:
             return launch_step_t<Real, MRT, 2>(d, d_descs, d_items, n_items, n_dom, parity, bx,
@@ -287,13 +298,13 @@ cudaError_t launch_step_w(const DomDesc& d, const DomDesc* d_descs, const WorkIt
 template <typename Real>
 int launch_step_prec(int coll, const DomDesc& d, const DomDesc* d_descs, const WorkItem* d_items,
                      int n_items, int n_dom, int parity, int bx, int rows, int band_mul, int grid_p,
-                     int* sched, void* stream)
+                     int* sched, bool one_body, void* stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return int(coll ? launch_step_w<Real, true>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                rows, band_mul, grid_p, sched, s)
+                                                rows, band_mul, grid_p, sched, one_body, s)
                     : launch_step_w<Real, false>(d, d_descs, d_items, n_items, n_dom, parity, bx,
-                                                 rows, band_mul, grid_p, sched, s));
+                                                 rows, band_mul, grid_p, sched, one_body, s));
 }
 
 // Resident CTAs per SM of the batched kernels (single: of the single-domain

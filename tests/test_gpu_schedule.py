@@ -85,6 +85,11 @@ def _schedules(lbf, compact):
         "multistep-overfilled-sealed": lbf.schedule([96, 160, 288], 32, ctas_per_sm=0,
                                                     max_nx=[w(96), w(160)], order=1,
                                                     persist=1, fill_pct=150, seal_edges=1),
+        # every compute-warp count 2..9, all classes on the one kernel body
+        # built for any width
+        "eight-class-ladder": lbf.schedule([64, 96, 128, 160, 192, 224, 256, 288], 16,
+                                           ctas_per_sm=0, order=1,
+                                           max_nx=[w(b) for b in (64, 96, 128, 160, 192, 224, 256)]),
         # whole-domain strips that write whole sectors (zeroed ghost columns)
         "sealed-ladder": lbf.schedule([96, 160, 288], 64, ctas_per_sm=0,
                                       max_nx=[w(96), w(160)], order=1, seal_edges=[1, 0, 1]),
@@ -97,10 +102,11 @@ MULTISTEP = ("multistep-ladder", "multistep-short-blocks", "multistep-few-ctas",
 
 @pytest.mark.parametrize("name", ["one-class-persistent", "one-item-per-cta-largest-first",
                                   "two-classes-chained", "two-classes-in-turn", "three-classes",
-                                  "empty-class", "sealed-ladder", *MULTISTEP])
+                                  "empty-class", "eight-class-ladder", "sealed-ladder",
+                                  *MULTISTEP])
 def test_schedule_gives_single_domain_results(lbf, single_states, name):
     compact, ref = single_states
-    if (name in MULTISTEP or name == "sealed-ladder") and not compact:
+    if (name in MULTISTEP or name in ("sealed-ladder", "eight-class-ladder")) and not compact:
         pytest.skip("persistent launches, sealing and 288-wide strips take compact storage")
     specs = _specs()
     plist = _plist(lbf, specs, compact)
