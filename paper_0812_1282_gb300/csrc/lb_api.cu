@@ -1879,7 +1879,8 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
         ladders = {{64, 128, 256}, {64, 128, 192, 256}};
     else
         ladders = {{64, 128}};
-    // seal: 0 none, 1 the narrowest class (the shortest rows), 2 every class
+    // seal: the classes of at most `seal` compute warps seal their rows (0
+    // none): the narrow strips, whose rows are short, gain the most from it
     auto ladder = [&](const std::vector<int>& lad, int r, int persist, int seal) {
         lb_schedule s{};
         s.n_class = int(lad.size());
@@ -1892,7 +1893,7 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
             s.rows[c] = r;
             s.ctas_per_sm[c] = 0;
             s.max_nx[c] = compact ? lbfe::compact_strip(lad[c]) : lad[c];
-            s.seal_edges[c] = seal == 2 || (seal == 1 && c == 0);
+            s.seal_edges[c] = lad[c] / 32 <= seal;
         }
         out.push_back(s);
     };
@@ -1900,11 +1901,11 @@ std::vector<lb_schedule> batch_candidates(const lb_handle* h)
         for (int r : {48, 64, 96, 128}) ladder(lad, r, 0, 0);
     if (compact && h->precision == LB_FP32)
         for (const auto& lad : ladders) {
-            // the same ladders with sealed rows, and as persistent launches
-            // (each class's steps in one launch, the GPU shared out between
-            // the classes)
-            for (int r : {32, 64})
-                for (int seal : {1, 2}) ladder(lad, r, 0, seal);
+            // the same ladders with sealed rows (strips up to 184 or 244
+            // columns, or all), and as persistent launches (each class's
+            // steps in one launch, the GPU shared out between the classes)
+            for (int r : {32, 64, 96})
+                for (int seal : {3, 4, 9}) ladder(lad, r, 0, seal);
             for (int r : {32, 64}) ladder(lad, r, 1, 0);
         }
     return out;
