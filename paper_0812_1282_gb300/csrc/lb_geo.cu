@@ -334,13 +334,27 @@ __device__ __forceinline__ void geo_tile_step(const DomDesc& D, int parity, int 
     }
 }
 
+// Programmatic dependent launch of the per-step kernel: once every CTA of
+// one step's grid has started, the next step's grid (launched with
+// programmatic stream serialisation) may be scheduled; its CTAs build their
+// tables from the static class map, then wait until the previous grid has
+// finished and its writes are visible before they touch the state.  The
+// next launch and its set-up so overlap the tail of this one.
+__device__ __forceinline__ void pdl_allow_next()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename Real, bool MRT>
 __global__ void __launch_bounds__(kGTX * kGTY) geo_step_kernel(DomDesc D, int parity)
 {
     __shared__ GeoTables t;
     __shared__ Real ph[kGPY][kGPX];
     const int x0 = blockIdx.x * kGTX, y0 = blockIdx.y * kGTY;
+    pdl_allow_next();
     geo_tile_setup(D, x0, y0, t);
+    pdl_wait_prev();
     geo_tile_step<Real, MRT, false>(D, parity, x0, y0, t, ph);
 }
 
@@ -688,9 +702,17 @@ dim3 geo_grid(const DomDesc& d) { return dim3((d.nx + kGeoBlock - 1) / kGeoBlock
 template <typename Real, bool MRT>
 cudaError_t geo_step_t(const DomDesc& d, int parity, cudaStream_t s)
 {
-    const dim3 grid((d.nx + kGTX - 1) / kGTX, (d.ny + kGTY - 1) / kGTY);
-    geo_step_kernel<Real, MRT><<<grid, kGTX * kGTY, 0, s>>>(d, parity);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((d.nx + kGTX - 1) / kGTX, (d.ny + kGTY - 1) / kGTY);
+    cfg.blockDim = dim3(kGTX * kGTY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, geo_step_kernel<Real, MRT>, d, parity);
 }
 
 template <typename Real, bool MRT>
