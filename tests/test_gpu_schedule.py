@@ -147,6 +147,37 @@ def test_autotune_keeps_state_and_picks_valid_schedule(lbf):
     other.close()
 
 
+def test_fp64_ladder_matches_single_domains(lbf):
+    """FP64 (full g storage): a two-class ladder, whose classes both launch
+    the one kernel body built for any width, and a single class on the body
+    built for its width give each domain's single-domain state bit for bit
+    (walls, 64- and 128-column strips, domains split over several strips)."""
+    specs = _specs()[:6]
+    plist = [lbf.params(**lbinputs.BASE, collision="mrt", precision="fp64",
+                        tau_alpha=s["tau_alpha"], tau_beta=s["tau_beta"],
+                        h_bottom=lbf.lb_wetting_h(s["theta"]), step2_relax_momentum=True)
+             for s in specs]
+    steps = 67
+    ref = []
+    for d, s in enumerate(specs):
+        sim = lbf.Lattice(plist[d], s["nx"], s["ny"])
+        sim.init_drop(s["R"], s["cx"], s["cy"])
+        sim.step(steps)
+        ref.append(sim.populations())
+        sim.close()
+    for sc in (lbf.schedule([64, 128], 16, ctas_per_sm=0, max_nx=[100], order=1),
+               lbf.schedule(128, 16, ctas_per_sm=0)):
+        batch = lbf.Batch(plist, [s["nx"] for s in specs], [s["ny"] for s in specs])
+        batch.set_schedule(sc)
+        for d, s in enumerate(specs):
+            batch.init_drop(s["R"], s["cx"], s["cy"], dom=d)
+        batch.step(steps)
+        for d in range(len(specs)):
+            fb, gb = batch.populations(dom=d)
+            assert np.array_equal(fb, ref[d][0]) and np.array_equal(gb, ref[d][1]), (sc.n_class, d)
+        batch.close()
+
+
 def test_schedule_validation(lbf):
     specs = _specs()[:3]
     plist = _plist(lbf, specs, True)
