@@ -455,9 +455,10 @@ def batch_params(lbf, specs, compact):
 
 
 # The eight-class ladder the autotuner picks for the 256 drops (strips of 120,
-# 184, 244, 308, 368, 432, 492 and 556 columns, 96 rows): a fixed schedule for
-# profiling runs.
+# 184, 244, 308, 368, 432, 492 and 556 columns, 96 rows, the rows of the three
+# narrowest classes sealed): a fixed schedule for profiling runs.
 LADDER_BX = (64, 96, 128, 160, 192, 224, 256, 288)
+LADDER_SEALED_UP_TO = 128
 
 
 # fixed batched schedules (--schedule): (rows per item, persistent launches)
@@ -468,7 +469,8 @@ def ladder_schedule(lbf, rows=64, persist=0):
     strip = lambda bx: (62 * (bx // 32) - 2) // 4 * 4
     return lbf.schedule(list(LADDER_BX), rows, ctas_per_sm=0,
                         max_nx=[strip(bx) for bx in LADDER_BX[:-1]], order=1, persist=persist,
-                        fill_pct=85 if persist else 0)
+                        fill_pct=85 if persist else 0,
+                        seal_edges=[int(bx <= LADDER_SEALED_UP_TO) for bx in LADDER_BX])
 
 
 # steps of the persistent-launch comparison on the batched workload
